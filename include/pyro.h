@@ -1,0 +1,207 @@
+/*
+ * pyro.h -- C ABI of libpyro: Swendsen-Wang multi-cluster sweeps of the
+ * ferromagnetic Ising, classical XY and classical Heisenberg models on the
+ * periodic pyrochlore lattice, on one GB300 GPU (sm_103a).
+ *
+ * The physics is that of Soldatov, Nefedev, Komura and Okabe, "Large-scale
+ * calculation of ferromagnetic spin systems on the pyrochlore lattice"
+ * (arXiv:1612.08312):
+ *   Sec. 2  lattice: L x L x L cubic cells of 16 sites, periodic boundaries,
+ *           N = 16 L^3 sites, coordination number six;
+ *   Eq. 1   H = -J sum_<ij> s_i . s_j, unit n-vectors, n = 1 (Ising),
+ *           2 (XY), 3 (Heisenberg);
+ *   Sec. 2  Swendsen-Wang multi-cluster update on one GPU, with Wolff's
+ *           embedded cluster (reflection about a random plane) for n = 2, 3;
+ *   Eq. 2   moment ratio U = <m^4>/<m^2>^2 with m = M/N.
+ *
+ * Conventions the paper leaves open, fixed here so that a run is a
+ * deterministic function of (L, model, start, seed, beta sequence):
+ *   site index   i = 16 (x + L (y + L z)) + 4 f + mu, position (quarter
+ *                cell units) 4 (x,y,z) + A_f + B_mu, A = {0,(0,2,2),(2,0,2),
+ *                (2,2,0)}, B = {0,(0,1,1),(1,0,1),(1,1,0)};
+ *   bond id      b = 12 r + k, r = i >> 2; k = 0..5 the pairs (0,1) (0,2)
+ *                (0,3) (1,2) (1,3) (2,3) of basis vertices of the tetrahedron
+ *                of FCC point r, k = 6..11 the same pairs of the other
+ *                tetrahedron through site 4r;
+ *   random words Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
+ *                (j_lo, j_hi, sweep, tag), word x = output x & 3 of call
+ *                j = x >> 2; tags 1 bond, 2 flip, 3 axis, 4 initial state
+ *                (sweep field 0xFFFFFFFF);
+ *   Ising bond   active iff s_i = s_j and w_b < floor((1 - exp(-2 beta J))
+ *                2^32);
+ *   n-vector     axis r drawn once per sweep; active iff p_i p_j > 0 and
+ *                (w_b + 1/2) 2^-32 < 1 - exp(-2 beta J p_i p_j), p_i = s_i.r;
+ *   cluster      canonical label = minimum site index in the cluster; the
+ *                cluster flips iff bit 31 of flip word (label) is 1;
+ *                n-vector flip s <- s - 2 (s.r) r, then s <- s/|s|;
+ *   measurement  after every sweep: E, m = |M|/N, m2 = m m, m4 = m2 m2,
+ *                accumulated in FP64 with Neumaier compensation.
+ *
+ * Error behaviour: every int-returning call returns PYRO_OK (0) or a
+ * negative PYRO_E_* code and sets a thread-local message readable with
+ * pyro_last_error().  No C++ exception crosses this interface.  Calls on
+ * one handle are not thread-safe; different handles are independent.
+ * Work is enqueued on the handle's CUDA stream; calls that return data to
+ * the host synchronise that stream first.  Device-side failures (a union-
+ * find or barrier wait that exceeded its bound) are recorded in a device
+ * status word and returned by the next synchronising call as
+ * PYRO_E_NOCONVERGE or PYRO_E_TIMEOUT.
+ */
+#ifndef PYRO_H
+#define PYRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pyro_ctx *pyro_handle;
+typedef struct pyro_batch_ctx *pyro_batch;
+
+enum { PYRO_ISING = 1, PYRO_XY = 2, PYRO_HEIS = 3 };
+enum { PYRO_FP32 = 0, PYRO_FP64 = 1 };
+enum { PYRO_START_UP = 0, PYRO_START_RANDOM = 1 };
+
+enum {
+    PYRO_OK = 0,
+    PYRO_E_INVAL = -1,      /* bad argument: L out of range, model, beta < 0 or NaN, n < 0, NULL */
+    PYRO_E_NOMEM = -2,      /* device or host allocation failed */
+    PYRO_E_CUDA = -3,       /* a CUDA runtime call failed (message has the CUDA error) */
+    PYRO_E_NOCONVERGE = -4, /* a union-find loop exceeded its iteration bound */
+    PYRO_E_TIMEOUT = -5,    /* a grid barrier wait exceeded its time bound */
+    PYRO_E_STATE = -6       /* call not valid in the current state */
+};
+
+/* Largest supported lattice: labels are int32 and N = 16 L^3 < 2^31. */
+#define PYRO_MAX_L 511
+
+typedef struct {
+    int L;             /* cells per edge, 1 <= L <= PYRO_MAX_L */
+    int model;         /* PYRO_ISING, PYRO_XY or PYRO_HEIS */
+    int precision;     /* n-vector spins: PYRO_FP32 or PYRO_FP64 (ignored for Ising) */
+    int start;         /* PYRO_START_UP (all +1 / e_x) or PYRO_START_RANDOM */
+    double J;          /* ferromagnetic coupling, J > 0 (the paper uses J = 1) */
+    uint64_t seed;     /* Philox key */
+    void *stream;      /* cudaStream_t to run on; NULL = the library creates one */
+    int tile[3];       /* labelling tile in cells (each must divide L); {0,0,0} = default */
+} pyro_config;
+
+typedef struct {
+    uint64_t count;    /* sweeps accumulated since the last reset */
+    double sum_E;      /* sum of E over those sweeps (Neumaier-compensated FP64) */
+    double sum_E2;     /* sum of E^2 */
+    double sum_m2;     /* sum of m^2 */
+    double sum_m4;     /* sum of m^4 */
+    double sum_absm;   /* sum of |m| */
+} pyro_stats_t;
+
+/* ---- single lattice ------------------------------------------------------ */
+
+/* Create a lattice with J = 1, FP32 n-vector spins, ordered start, a
+ * library-owned stream and the default tile.  *out receives the handle,
+ * owned by the caller until pyro_destroy.  Sec. 2 (lattice), Eq. 1. */
+int pyro_init(pyro_handle *out, int L, int model, uint64_t seed);
+
+/* Same with every option of pyro_config.  cfg is read, not kept. */
+int pyro_init_ex(pyro_handle *out, const pyro_config *cfg);
+
+/* Enqueue n Swendsen-Wang sweeps at inverse temperature beta (Sec. 2) on
+ * the handle's stream; each sweep is followed by the measurement of Eq. 2,
+ * accumulated into the statistics.  Asynchronous: returns after enqueueing.
+ * beta >= 0 and finite, n >= 0. */
+int pyro_sweep(pyro_handle h, double beta, int n);
+
+/* Instantaneous E, m^2, m^4 of the current configuration (Eq. 1, Eq. 2).
+ * Synchronises the stream.  Any pointer may be NULL. */
+int pyro_measure(pyro_handle h, double *E, double *m2, double *m4);
+
+/* Accumulated statistics since the last reset (Eq. 2 moments and energy).
+ * Synchronises the stream. */
+int pyro_stats(pyro_handle h, pyro_stats_t *s);
+int pyro_reset_stats(pyro_handle h);
+
+/* Spins in canonical site order, host memory, synchronous.
+ * Ising: N int8 values +1/-1 (bytes = N).  n-vector: N x n doubles,
+ * site-major (bytes = 8 n N); the FP32 store rounds them to float.
+ * bytes must equal the exact size. */
+int pyro_get_spins(pyro_handle h, void *host, size_t bytes);
+int pyro_set_spins(pyro_handle h, const void *host, size_t bytes);
+
+/* The library's compact device layout of the spins, copied to/from host
+ * memory (pinned memory gives full bandwidth):
+ *   Ising:   one uint16 per cell, bit (i & 15) of word (i >> 4) is 1 iff
+ *            s_i = -1 (bytes = N / 8);
+ *   n-vector: n component planes of N floats (FP32) or doubles (FP64).
+ * pyro_state_bytes gives the size.  Enqueued on the handle's stream; the
+ * host buffer must stay valid until the stream is synchronised. */
+size_t pyro_state_bytes(pyro_handle h);
+int pyro_get_state(pyro_handle h, void *host, size_t bytes);
+int pyro_set_state(pyro_handle h, const void *host, size_t bytes);
+
+/* Canonical cluster labels of the last sweep (the minimum site index of
+ * each site's cluster), N int32 values.  Synchronises. */
+int pyro_get_labels(pyro_handle h, int32_t *host, size_t bytes);
+
+/* Sweep counter: the sweep field of the Philox counter of the next sweep. */
+int pyro_get_sweep(pyro_handle h, uint64_t *sweep);
+int pyro_set_sweep(pyro_handle h, uint64_t sweep);
+
+/* Per-sweep trace: keep the last `capacity` sweeps' (E, m2, m4, M_x)
+ * records in a device ring buffer (0 disables).  pyro_get_trace copies the
+ * most recent min(count, capacity) records, oldest first, as 4 doubles
+ * each, and returns their number through *n. */
+int pyro_set_trace(pyro_handle h, int64_t capacity);
+int pyro_get_trace(pyro_handle h, double *host, int64_t max_records, int64_t *n);
+
+/* Wait for all enqueued work; report any device-side status. */
+int pyro_sync(pyro_handle h);
+
+/* Facts about a handle. */
+int64_t pyro_num_sites(pyro_handle h);
+int pyro_get_tile(pyro_handle h, int tile[3]);
+void *pyro_get_stream(pyro_handle h);
+
+/* Number of kernel launches this handle has issued (for accounting). */
+uint64_t pyro_launch_count(pyro_handle h);
+
+/* Tracing: run n sweeps at beta like pyro_sweep, but as separate launches
+ * bracketed by CUDA events, and return the mean device time in ms of each
+ * of the five phases of a sweep in phase_ms[0..4]: tile-local labelling
+ * (with bond activation), tile-crossing unions, flip, measurement,
+ * accumulation.  Synchronises.  The chain advances exactly as with
+ * pyro_sweep. */
+#define PYRO_NPHASE 5
+int pyro_profile_phases(pyro_handle h, double beta, int n, double *phase_ms);
+
+void pyro_destroy(pyro_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pyro_last_error(void);
+
+/* ---- batched replicas ----------------------------------------------------- */
+
+/* R independent lattices of sizes L[r] at inverse temperatures beta[r],
+ * one model and precision, updated together: every phase of a sweep is one
+ * launch over all replicas' tiles, and a multi-sweep call is a CUDA graph.
+ * Replica r uses seed + r * 0x9E3779B97F4A7C15 (mod 2^64), so it is the
+ * same chain as a single lattice created with that seed.  start as in
+ * pyro_config.  Independent runs (Sec. 2: five independent runs). */
+int pyro_batch_init(pyro_batch *out, int R, const int *L, const double *beta, int model,
+                    int precision, int start, uint64_t seed);
+int pyro_batch_sweep(pyro_batch b, int n);
+int pyro_batch_stats(pyro_batch b, int r, pyro_stats_t *s);
+int pyro_batch_reset_stats(pyro_batch b);
+int pyro_batch_measure(pyro_batch b, int r, double *E, double *m2, double *m4);
+int pyro_batch_get_spins(pyro_batch b, int r, void *host, size_t bytes);
+int pyro_batch_sync(pyro_batch b);
+int64_t pyro_batch_total_sites(pyro_batch b);
+uint64_t pyro_batch_launch_count(pyro_batch b);
+void pyro_batch_destroy(pyro_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PYRO_H */

@@ -1,0 +1,419 @@
+"""GB300-native Swendsen-Wang sweeps on the pyrochlore lattice.
+
+A thin ctypes binding of libpyro (include/pyro.h), the CUDA library that
+runs the whole sweep on the GPU: bond activation, connected-component
+labelling, cluster flips and the E / m^2 / m^4 reductions of Soldatov,
+Nefedev, Komura and Okabe (arXiv:1612.08312, Sec. 2, Eq. 1-2).
+
+The functions below carry the C names and only marshal arguments; every step
+of a sweep runs in the library's kernels.  There is no CPU fallback: if the
+library cannot be built or loaded, importing raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ISING, XY, HEIS = 1, 2, 3
+FP32, FP64 = 0, 1
+START_UP, START_RANDOM = 0, 1
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_NOCONVERGE, E_TIMEOUT, E_STATE = 0, -1, -2, -3, -4, -5, -6
+MAX_L = 511
+MAX_REPS = 64
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PyroError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pyro error {code}: {msg}")
+        self.code = code
+
+
+class pyro_config(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("model", ctypes.c_int), ("precision", ctypes.c_int),
+                ("start", ctypes.c_int), ("J", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int * 3)]
+
+
+class pyro_stats_t(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("sum_E", ctypes.c_double), ("sum_E2", ctypes.c_double),
+                ("sum_m2", ctypes.c_double), ("sum_m4", ctypes.c_double), ("sum_absm", ctypes.c_double)]
+
+
+_SIGS = {
+    "pyro_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
+    "pyro_init_ex": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(pyro_config)]),
+    "pyro_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
+    "pyro_measure": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_double)] * 3),
+    "pyro_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pyro_stats_t)]),
+    "pyro_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
+    "pyro_get_spins": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "pyro_set_spins": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "pyro_state_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "pyro_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "pyro_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "pyro_get_labels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "pyro_get_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "pyro_set_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "pyro_set_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "pyro_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "pyro_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "pyro_num_sites": (ctypes.c_int64, [ctypes.c_void_p]),
+    "pyro_get_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "pyro_get_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
+    "pyro_launch_count": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "pyro_profile_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "pyro_destroy": (None, [ctypes.c_void_p]),
+    "pyro_last_error": (ctypes.c_char_p, []),
+    "pyro_batch_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
+    "pyro_batch_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "pyro_batch_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(pyro_stats_t)]),
+    "pyro_batch_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
+    "pyro_batch_measure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_double)] * 3),
+    "pyro_batch_get_spins": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
+    "pyro_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "pyro_batch_total_sites": (ctypes.c_int64, [ctypes.c_void_p]),
+    "pyro_batch_launch_count": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "pyro_batch_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def library_path() -> str:
+    return _build.OUT
+
+
+def lib():
+    """Load libpyro.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def declared_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise PyroError(rc, lib().pyro_last_error().decode())
+
+
+def _buf(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------- C names --
+def pyro_init(L: int, model: int, seed: int):
+    h = ctypes.c_void_p()
+    _check(lib().pyro_init(ctypes.byref(h), L, model, seed))
+    return h
+
+
+def pyro_init_ex(L: int, model: int, seed: int, precision: int = FP32, start: int = START_UP,
+                 J: float = 1.0, stream: int | None = None, tile=(0, 0, 0)):
+    cfg = pyro_config(L, model, precision, start, J, seed, stream, (ctypes.c_int * 3)(*tile))
+    h = ctypes.c_void_p()
+    _check(lib().pyro_init_ex(ctypes.byref(h), ctypes.byref(cfg)))
+    return h
+
+
+def pyro_sweep(h, beta: float, n: int = 1):
+    _check(lib().pyro_sweep(h, beta, n))
+
+
+def pyro_measure(h):
+    E, m2, m4 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().pyro_measure(h, ctypes.byref(E), ctypes.byref(m2), ctypes.byref(m4)))
+    return E.value, m2.value, m4.value
+
+
+def _stats_dict(s: pyro_stats_t) -> dict:
+    return dict(count=int(s.count), sum_E=s.sum_E, sum_E2=s.sum_E2, sum_m2=s.sum_m2, sum_m4=s.sum_m4,
+                sum_absm=s.sum_absm)
+
+
+def pyro_stats(h) -> dict:
+    s = pyro_stats_t()
+    _check(lib().pyro_stats(h, ctypes.byref(s)))
+    return _stats_dict(s)
+
+
+def pyro_reset_stats(h):
+    _check(lib().pyro_reset_stats(h))
+
+
+def pyro_num_sites(h) -> int:
+    return int(lib().pyro_num_sites(h))
+
+
+def pyro_get_spins(h, model: int) -> np.ndarray:
+    N = pyro_num_sites(h)
+    out = np.zeros(N, dtype=np.int8) if model == ISING else np.zeros((N, model), dtype=np.float64)
+    _check(lib().pyro_get_spins(h, _buf(out), out.nbytes))
+    return out
+
+
+def pyro_set_spins(h, spins: np.ndarray):
+    a = np.ascontiguousarray(spins)
+    if a.dtype != np.int8:
+        a = np.ascontiguousarray(a, dtype=np.float64)
+    _check(lib().pyro_set_spins(h, _buf(a), a.nbytes))
+
+
+def pyro_state_bytes(h) -> int:
+    return int(lib().pyro_state_bytes(h))
+
+
+def pyro_get_state(h, host_ptr: int, nbytes: int):
+    """Copy the compact device state to host memory at host_ptr (asynchronous)."""
+    _check(lib().pyro_get_state(h, ctypes.c_void_p(host_ptr), nbytes))
+
+
+def pyro_set_state(h, host_ptr: int, nbytes: int):
+    _check(lib().pyro_set_state(h, ctypes.c_void_p(host_ptr), nbytes))
+
+
+def pyro_get_labels(h) -> np.ndarray:
+    out = np.zeros(pyro_num_sites(h), dtype=np.int32)
+    _check(lib().pyro_get_labels(h, _buf(out), out.nbytes))
+    return out
+
+
+def pyro_get_sweep(h) -> int:
+    s = ctypes.c_uint64()
+    _check(lib().pyro_get_sweep(h, ctypes.byref(s)))
+    return int(s.value)
+
+
+def pyro_set_sweep(h, sweep: int):
+    _check(lib().pyro_set_sweep(h, sweep))
+
+
+def pyro_set_trace(h, capacity: int):
+    _check(lib().pyro_set_trace(h, capacity))
+
+
+def pyro_get_trace(h, max_records: int) -> np.ndarray:
+    out = np.zeros((max(max_records, 1), 4), dtype=np.float64)
+    n = ctypes.c_int64()
+    _check(lib().pyro_get_trace(h, _buf(out), max_records, ctypes.byref(n)))
+    return out[: n.value]
+
+
+def pyro_sync(h):
+    _check(lib().pyro_sync(h))
+
+
+def pyro_get_tile(h):
+    t = (ctypes.c_int * 3)()
+    _check(lib().pyro_get_tile(h, t))
+    return tuple(t)
+
+
+def pyro_get_stream(h) -> int:
+    return lib().pyro_get_stream(h) or 0
+
+
+def pyro_launch_count(h) -> int:
+    return int(lib().pyro_launch_count(h))
+
+
+PHASES = ("local", "boundary", "flip", "measure", "accumulate")
+
+
+def pyro_profile_phases(h, beta: float, n: int) -> dict:
+    """Mean device ms of each sweep phase over n event-bracketed sweeps."""
+    ms = (ctypes.c_double * len(PHASES))()
+    _check(lib().pyro_profile_phases(h, beta, n, ms))
+    return dict(zip(PHASES, list(ms)))
+
+
+def pyro_destroy(h):
+    lib().pyro_destroy(h)
+
+
+def pyro_last_error() -> str:
+    return lib().pyro_last_error().decode()
+
+
+def pyro_batch_init(Ls, betas, model: int, precision: int = FP32, start: int = START_RANDOM, seed: int = 1):
+    R = len(Ls)
+    La = (ctypes.c_int * R)(*Ls)
+    Ba = (ctypes.c_double * R)(*betas)
+    b = ctypes.c_void_p()
+    _check(lib().pyro_batch_init(ctypes.byref(b), R, La, Ba, model, precision, start, seed))
+    return b
+
+
+def pyro_batch_sweep(b, n: int = 1):
+    _check(lib().pyro_batch_sweep(b, n))
+
+
+def pyro_batch_stats(b, r: int) -> dict:
+    s = pyro_stats_t()
+    _check(lib().pyro_batch_stats(b, r, ctypes.byref(s)))
+    return _stats_dict(s)
+
+
+def pyro_batch_reset_stats(b):
+    _check(lib().pyro_batch_reset_stats(b))
+
+
+def pyro_batch_measure(b, r: int):
+    E, m2, m4 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().pyro_batch_measure(b, r, ctypes.byref(E), ctypes.byref(m2), ctypes.byref(m4)))
+    return E.value, m2.value, m4.value
+
+
+def pyro_batch_get_spins(b, r: int, N: int, model: int) -> np.ndarray:
+    out = np.zeros(N, dtype=np.int8) if model == ISING else np.zeros((N, model), dtype=np.float64)
+    _check(lib().pyro_batch_get_spins(b, r, _buf(out), out.nbytes))
+    return out
+
+
+def pyro_batch_sync(b):
+    _check(lib().pyro_batch_sync(b))
+
+
+def pyro_batch_total_sites(b) -> int:
+    return int(lib().pyro_batch_total_sites(b))
+
+
+def pyro_batch_launch_count(b) -> int:
+    return int(lib().pyro_batch_launch_count(b))
+
+
+def pyro_batch_destroy(b):
+    lib().pyro_batch_destroy(b)
+
+
+# ------------------------------------------------------- convenience API --
+class Lattice:
+    """One pyrochlore lattice on the GPU (owns a pyro_handle)."""
+
+    def __init__(self, L: int, model: int = ISING, seed: int = 1, precision: int = FP32,
+                 start: str | int = "up", J: float = 1.0, tile=(0, 0, 0), stream: int | None = None):
+        st = start if isinstance(start, int) else (START_RANDOM if start == "random" else START_UP)
+        self.L, self.model, self.seed, self.precision = L, model, seed, precision
+        self.h = pyro_init_ex(L, model, seed, precision, st, J, stream, tile)
+        self.N = pyro_num_sites(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pyro_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, beta: float, n: int = 1):
+        pyro_sweep(self.h, beta, n)
+
+    def measure(self):
+        return pyro_measure(self.h)
+
+    def stats(self):
+        return pyro_stats(self.h)
+
+    def reset_stats(self):
+        pyro_reset_stats(self.h)
+
+    def spins(self):
+        return pyro_get_spins(self.h, self.model)
+
+    def set_spins(self, s):
+        pyro_set_spins(self.h, s)
+
+    def labels(self):
+        return pyro_get_labels(self.h)
+
+    @property
+    def sweep_count(self):
+        return pyro_get_sweep(self.h)
+
+    @sweep_count.setter
+    def sweep_count(self, s):
+        pyro_set_sweep(self.h, s)
+
+    def sync(self):
+        pyro_sync(self.h)
+
+    @property
+    def tile(self):
+        return pyro_get_tile(self.h)
+
+    @property
+    def launches(self):
+        return pyro_launch_count(self.h)
+
+
+class Replicas:
+    """Independent lattices updated together (owns a pyro_batch)."""
+
+    def __init__(self, Ls, betas, model: int = ISING, precision: int = FP32, start: str | int = "random",
+                 seed: int = 1):
+        st = start if isinstance(start, int) else (START_RANDOM if start == "random" else START_UP)
+        self.Ls, self.betas, self.model = list(Ls), list(betas), model
+        self.b = pyro_batch_init(self.Ls, self.betas, model, precision, st, seed)
+        self.total_sites = pyro_batch_total_sites(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            pyro_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n: int = 1):
+        pyro_batch_sweep(self.b, n)
+
+    def stats(self, r: int):
+        return pyro_batch_stats(self.b, r)
+
+    def reset_stats(self):
+        pyro_batch_reset_stats(self.b)
+
+    def measure(self, r: int):
+        return pyro_batch_measure(self.b, r)
+
+    def spins(self, r: int):
+        return pyro_batch_get_spins(self.b, r, 16 * self.Ls[r] ** 3, self.model)
+
+    def sync(self):
+        pyro_batch_sync(self.b)
+
+    @property
+    def launches(self):
+        return pyro_batch_launch_count(self.b)
+
+
+def replica_seed(seed: int, r: int) -> int:
+    """Seed of replica r of a batch: seed + r * 0x9E3779B97F4A7C15 mod 2^64."""
+    return (seed + r * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF

@@ -1,0 +1,434 @@
+// api.cu -- the C ABI of libpyro (include/pyro.h): argument checking, error
+// reporting and host-side layout conversion around the Engine.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace pyro {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+static int fail(int code, const std::string &msg)
+{
+    set_error(msg);
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const std::string &what)
+{
+    return fail(PYRO_E_CUDA, what + ": " + cudaGetErrorString(e));
+}
+
+#define PYRO_CUDA(call, what)                               \
+    do {                                                    \
+        const cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+    } while (0)
+
+static int finish(Engine &e)
+{
+    std::string err;
+    const int st = e.read_status(err);
+    if (st < 0) return fail(PYRO_E_CUDA, err);
+    if (st & ST_NOCONVERGE) return fail(PYRO_E_NOCONVERGE, "union-find exceeded its iteration bound");
+    if (st & ST_TIMEOUT) return fail(PYRO_E_TIMEOUT, "a device wait exceeded its time bound");
+    return PYRO_OK;
+}
+
+static bool beta_ok(double b) { return b >= 0.0 && std::isfinite(b); }
+
+static int create(Engine &e, int R, const int *Ls, const double *betas, int model, int prec, int start, double J,
+                  const uint64_t *seeds, void *stream, const int tile[3])
+{
+    if (R < 1 || R > MAX_REPS) return fail(PYRO_E_INVAL, "number of replicas must be in [1, 64]");
+    for (int r = 0; r < R; ++r) {
+        if (Ls[r] < 1 || Ls[r] > PYRO_MAX_L) return fail(PYRO_E_INVAL, "L must be in [1, 511]");
+        if (betas && !beta_ok(betas[r])) return fail(PYRO_E_INVAL, "beta must be finite and >= 0");
+    }
+    if (model < PYRO_ISING || model > PYRO_HEIS) return fail(PYRO_E_INVAL, "model must be 1, 2 or 3");
+    if (prec != PYRO_FP32 && prec != PYRO_FP64) return fail(PYRO_E_INVAL, "precision must be PYRO_FP32 or PYRO_FP64");
+    if (start != PYRO_START_UP && start != PYRO_START_RANDOM)
+        return fail(PYRO_E_INVAL, "start must be PYRO_START_UP or PYRO_START_RANDOM");
+    if (!(J > 0.0) || !std::isfinite(J)) return fail(PYRO_E_INVAL, "J must be positive and finite");
+    TileShape t = default_tile(Ls, R, model);
+    if (tile && (tile[0] || tile[1] || tile[2])) t = TileShape{tile[0], tile[1], tile[2]};
+    const std::string why = check_tile(Ls, R, model, prec, t);
+    if (!why.empty()) return fail(PYRO_E_INVAL, why);
+    std::string err;
+    const cudaError_t ce = e.setup(R, Ls, betas, model, prec, start, J, seeds, static_cast<cudaStream_t>(stream), t, err);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        e.release();
+        if (ce == cudaErrorMemoryAllocation) return fail(PYRO_E_NOMEM, err + ": " + cudaGetErrorString(ce));
+        return cuda_fail(ce, err);
+    }
+    return PYRO_OK;
+}
+
+static size_t vec_elem(const Engine &e) { return e.prec == PYRO_FP64 ? 8 : 4; }
+
+static int get_spins(Engine &e, int r, void *host, size_t bytes)
+{
+    const int64_t N = e.reps[r].N;
+    if (e.model == PYRO_ISING) {
+        if (bytes != (size_t)N) return fail(PYRO_E_INVAL, "Ising spins need N bytes");
+        std::vector<uint16_t> w((size_t)(N / 16));
+        PYRO_CUDA(cudaMemcpyAsync(w.data(), e.reps[r].spins, w.size() * 2, cudaMemcpyDeviceToHost, e.stream), "spins copy");
+        PYRO_CUDA(cudaStreamSynchronize(e.stream), "stream synchronize");
+        int8_t *o = static_cast<int8_t *>(host);
+        for (int64_t i = 0; i < N; ++i) o[i] = ((w[i >> 4] >> (i & 15)) & 1) ? -1 : 1;
+        return PYRO_OK;
+    }
+    const int n = e.model;
+    if (bytes != (size_t)N * n * sizeof(double)) return fail(PYRO_E_INVAL, "n-vector spins need 8 n N bytes");
+    std::vector<unsigned char> raw((size_t)N * n * vec_elem(e));
+    PYRO_CUDA(cudaMemcpyAsync(raw.data(), e.reps[r].spins, raw.size(), cudaMemcpyDeviceToHost, e.stream), "spins copy");
+    PYRO_CUDA(cudaStreamSynchronize(e.stream), "stream synchronize");
+    double *o = static_cast<double *>(host);
+    for (int64_t i = 0; i < N; ++i)
+        for (int k = 0; k < n; ++k)
+            o[i * n + k] = e.prec == PYRO_FP64 ? reinterpret_cast<const double *>(raw.data())[(size_t)k * N + i]
+                                               : (double)reinterpret_cast<const float *>(raw.data())[(size_t)k * N + i];
+    return PYRO_OK;
+}
+
+static int stats_of(Engine &e, int r, pyro_stats_t *s)
+{
+    DevStats d;
+    PYRO_CUDA(cudaMemcpyAsync(&d, e.reps[r].st, sizeof(d), cudaMemcpyDeviceToHost, e.stream), "stats copy");
+    const int rc = finish(e);
+    if (rc) return rc;
+    s->count = d.count;
+    double *dst[5] = {&s->sum_E, &s->sum_E2, &s->sum_m2, &s->sum_m4, &s->sum_absm};
+    for (int k = 0; k < 5; ++k) *dst[k] = d.acc_s[k] + d.acc_c[k];
+    return PYRO_OK;
+}
+
+static int reset_stats(Engine &e)
+{
+    for (int r = 0; r < e.R; ++r) {
+        DevStats *d = e.reps[r].st;
+        PYRO_CUDA(cudaMemsetAsync(d->acc_s, 0, sizeof(d->acc_s), e.stream), "reset");
+        PYRO_CUDA(cudaMemsetAsync(d->acc_c, 0, sizeof(d->acc_c), e.stream), "reset");
+        PYRO_CUDA(cudaMemsetAsync(&d->count, 0, sizeof(d->count), e.stream), "reset");
+    }
+    return PYRO_OK;
+}
+
+static int measure_of(Engine &e, int r, double *E, double *m2, double *m4)
+{
+    PYRO_CUDA(e.measure(), "measure launch");
+    double last[4];
+    PYRO_CUDA(cudaMemcpyAsync(last, e.reps[r].st->last, sizeof(last), cudaMemcpyDeviceToHost, e.stream), "measure copy");
+    const int rc = finish(e);
+    if (rc) return rc;
+    if (E) *E = last[0];
+    if (m2) *m2 = last[1];
+    if (m4) *m4 = last[2];
+    return PYRO_OK;
+}
+
+}  // namespace pyro
+
+using namespace pyro;
+
+extern "C" {
+
+const char *pyro_last_error(void) { return g_err.c_str(); }
+
+int pyro_init_ex(pyro_handle *out, const pyro_config *cfg)
+{
+    if (!out || !cfg) return fail(PYRO_E_INVAL, "NULL argument");
+    *out = nullptr;
+    pyro_ctx *h = new (std::nothrow) pyro_ctx();
+    if (!h) return fail(PYRO_E_NOMEM, "host allocation failed");
+    const double beta0 = 0.0;
+    const int rc = create(h->e, 1, &cfg->L, &beta0, cfg->model, cfg->precision, cfg->start, cfg->J, &cfg->seed,
+                          cfg->stream, cfg->tile);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PYRO_OK;
+}
+
+int pyro_init(pyro_handle *out, int L, int model, uint64_t seed)
+{
+    pyro_config cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.L = L;
+    cfg.model = model;
+    cfg.precision = PYRO_FP32;
+    cfg.start = PYRO_START_UP;
+    cfg.J = 1.0;
+    cfg.seed = seed;
+    return pyro_init_ex(out, &cfg);
+}
+
+int pyro_sweep(pyro_handle h, double beta, int n)
+{
+    if (!h) return fail(PYRO_E_INVAL, "NULL handle");
+    if (!beta_ok(beta)) return fail(PYRO_E_INVAL, "beta must be finite and >= 0");
+    if (n < 0) return fail(PYRO_E_INVAL, "n must be >= 0");
+    if (n == 0) return PYRO_OK;
+    PYRO_CUDA(h->e.set_beta(0, beta), "parameter update");
+    PYRO_CUDA(h->e.sweeps(n), "sweep launch");
+    return PYRO_OK;
+}
+
+int pyro_measure(pyro_handle h, double *E, double *m2, double *m4)
+{
+    if (!h) return fail(PYRO_E_INVAL, "NULL handle");
+    return measure_of(h->e, 0, E, m2, m4);
+}
+
+int pyro_stats(pyro_handle h, pyro_stats_t *s)
+{
+    if (!h || !s) return fail(PYRO_E_INVAL, "NULL argument");
+    return stats_of(h->e, 0, s);
+}
+
+int pyro_reset_stats(pyro_handle h)
+{
+    if (!h) return fail(PYRO_E_INVAL, "NULL handle");
+    return reset_stats(h->e);
+}
+
+size_t pyro_state_bytes(pyro_handle h) { return h ? h->e.spin_bytes(0) : 0; }
+
+int pyro_get_state(pyro_handle h, void *host, size_t bytes)
+{
+    if (!h || !host) return fail(PYRO_E_INVAL, "NULL argument");
+    if (bytes != h->e.spin_bytes(0)) return fail(PYRO_E_INVAL, "state size mismatch");
+    PYRO_CUDA(cudaMemcpyAsync(host, h->e.reps[0].spins, bytes, cudaMemcpyDeviceToHost, h->e.stream), "state copy");
+    return PYRO_OK;
+}
+
+int pyro_set_state(pyro_handle h, const void *host, size_t bytes)
+{
+    if (!h || !host) return fail(PYRO_E_INVAL, "NULL argument");
+    if (bytes != h->e.spin_bytes(0)) return fail(PYRO_E_INVAL, "state size mismatch");
+    PYRO_CUDA(cudaMemcpyAsync(h->e.reps[0].spins, host, bytes, cudaMemcpyHostToDevice, h->e.stream), "state copy");
+    h->e.labels_valid = false;
+    return PYRO_OK;
+}
+
+int pyro_get_spins(pyro_handle h, void *host, size_t bytes)
+{
+    if (!h || !host) return fail(PYRO_E_INVAL, "NULL argument");
+    return get_spins(h->e, 0, host, bytes);
+}
+
+int pyro_set_spins(pyro_handle h, const void *host, size_t bytes)
+{
+    if (!h || !host) return fail(PYRO_E_INVAL, "NULL argument");
+    Engine &e = h->e;
+    const int64_t N = e.reps[0].N;
+    if (e.model == PYRO_ISING) {
+        if (bytes != (size_t)N) return fail(PYRO_E_INVAL, "Ising spins need N bytes");
+        const int8_t *s = static_cast<const int8_t *>(host);
+        std::vector<uint16_t> w((size_t)(N / 16), 0);
+        for (int64_t i = 0; i < N; ++i) {
+            if (s[i] != 1 && s[i] != -1) return fail(PYRO_E_INVAL, "Ising spins must be +1 or -1");
+            if (s[i] == -1) w[i >> 4] |= (uint16_t)(1u << (i & 15));
+        }
+        PYRO_CUDA(cudaMemcpyAsync(e.reps[0].spins, w.data(), w.size() * 2, cudaMemcpyHostToDevice, e.stream), "spins copy");
+        PYRO_CUDA(cudaStreamSynchronize(e.stream), "stream synchronize");
+    } else {
+        const int n = e.model;
+        if (bytes != (size_t)N * n * sizeof(double)) return fail(PYRO_E_INVAL, "n-vector spins need 8 n N bytes");
+        const double *s = static_cast<const double *>(host);
+        std::vector<unsigned char> raw((size_t)N * n * vec_elem(e));
+        for (int64_t i = 0; i < N; ++i)
+            for (int k = 0; k < n; ++k) {
+                if (e.prec == PYRO_FP64) reinterpret_cast<double *>(raw.data())[(size_t)k * N + i] = s[i * n + k];
+                else reinterpret_cast<float *>(raw.data())[(size_t)k * N + i] = (float)s[i * n + k];
+            }
+        PYRO_CUDA(cudaMemcpyAsync(e.reps[0].spins, raw.data(), raw.size(), cudaMemcpyHostToDevice, e.stream), "spins copy");
+        PYRO_CUDA(cudaStreamSynchronize(e.stream), "stream synchronize");
+    }
+    e.labels_valid = false;
+    return PYRO_OK;
+}
+
+int pyro_get_labels(pyro_handle h, int32_t *host, size_t bytes)
+{
+    if (!h || !host) return fail(PYRO_E_INVAL, "NULL argument");
+    if (bytes != (size_t)h->e.reps[0].N * sizeof(int32_t)) return fail(PYRO_E_INVAL, "labels need 4 N bytes");
+    if (!h->e.labels_valid) return fail(PYRO_E_STATE, "no sweep since the spins were last set");
+    PYRO_CUDA(cudaMemcpyAsync(host, h->e.reps[0].P, bytes, cudaMemcpyDeviceToHost, h->e.stream), "labels copy");
+    return finish(h->e);
+}
+
+int pyro_get_sweep(pyro_handle h, uint64_t *sweep)
+{
+    if (!h || !sweep) return fail(PYRO_E_INVAL, "NULL argument");
+    *sweep = h->e.sweep;
+    return PYRO_OK;
+}
+
+int pyro_set_sweep(pyro_handle h, uint64_t sweep)
+{
+    if (!h) return fail(PYRO_E_INVAL, "NULL handle");
+    PYRO_CUDA(h->e.set_sweep(sweep), "sweep update");
+    return PYRO_OK;
+}
+
+int pyro_set_trace(pyro_handle h, int64_t capacity)
+{
+    if (!h || capacity < 0) return fail(PYRO_E_INVAL, "bad argument");
+    const cudaError_t e = h->e.set_trace(0, capacity);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(PYRO_E_NOMEM, "trace allocation failed");
+    }
+    PYRO_CUDA(e, "trace setup");
+    return PYRO_OK;
+}
+
+int pyro_get_trace(pyro_handle h, double *host, int64_t max_records, int64_t *n)
+{
+    if (!h || !host || !n || max_records < 0) return fail(PYRO_E_INVAL, "bad argument");
+    *n = 0;
+    Engine &e = h->e;
+    const int64_t cap = e.reps[0].trace_cap;
+    if (!cap) return PYRO_OK;
+    unsigned long long count = 0;
+    PYRO_CUDA(cudaMemcpyAsync(&count, &e.reps[0].st->count, sizeof(count), cudaMemcpyDeviceToHost, e.stream), "count");
+    const int rc = finish(e);
+    if (rc) return rc;
+    const int64_t have = (int64_t)std::min<unsigned long long>(count, (unsigned long long)cap);
+    const int64_t take = std::min<int64_t>(have, max_records);
+    std::vector<double> all((size_t)cap * 4);
+    PYRO_CUDA(cudaMemcpyAsync(all.data(), e.reps[0].trace, all.size() * sizeof(double), cudaMemcpyDeviceToHost, e.stream),
+              "trace copy");
+    PYRO_CUDA(cudaStreamSynchronize(e.stream), "stream synchronize");
+    for (int64_t q = 0; q < take; ++q) {
+        const unsigned long long c = count - (unsigned long long)take + (unsigned long long)q;
+        std::memcpy(host + 4 * q, all.data() + 4 * (c % (unsigned long long)cap), 4 * sizeof(double));
+    }
+    *n = take;
+    return PYRO_OK;
+}
+
+int pyro_sync(pyro_handle h)
+{
+    if (!h) return fail(PYRO_E_INVAL, "NULL handle");
+    return finish(h->e);
+}
+
+int64_t pyro_num_sites(pyro_handle h) { return h ? h->e.reps[0].N : 0; }
+
+int pyro_get_tile(pyro_handle h, int tile[3])
+{
+    if (!h || !tile) return fail(PYRO_E_INVAL, "NULL argument");
+    tile[0] = h->e.tile.TX;
+    tile[1] = h->e.tile.TY;
+    tile[2] = h->e.tile.TZ;
+    return PYRO_OK;
+}
+
+void *pyro_get_stream(pyro_handle h) { return h ? (void *)h->e.stream : nullptr; }
+
+uint64_t pyro_launch_count(pyro_handle h) { return h ? h->e.launches : 0; }
+
+int pyro_profile_phases(pyro_handle h, double beta, int n, double *phase_ms)
+{
+    if (!h || !phase_ms) return fail(PYRO_E_INVAL, "NULL argument");
+    if (!beta_ok(beta)) return fail(PYRO_E_INVAL, "beta must be finite and >= 0");
+    if (n < 1) return fail(PYRO_E_INVAL, "n must be >= 1");
+    PYRO_CUDA(h->e.set_beta(0, beta), "parameter update");
+    PYRO_CUDA(h->e.profile(n, phase_ms), "profiled sweep");
+    return finish(h->e);
+}
+
+void pyro_destroy(pyro_handle h)
+{
+    if (!h) return;
+    h->e.release();
+    delete h;
+}
+
+// ------------------------------------------------------------- batches --
+int pyro_batch_init(pyro_batch *out, int R, const int *L, const double *beta, int model, int precision, int start,
+                    uint64_t seed)
+{
+    if (!out || !L || !beta) return fail(PYRO_E_INVAL, "NULL argument");
+    *out = nullptr;
+    if (R < 1 || R > MAX_REPS) return fail(PYRO_E_INVAL, "number of replicas must be in [1, 64]");
+    std::vector<uint64_t> seeds((size_t)R);
+    for (int r = 0; r < R; ++r) seeds[r] = seed + (uint64_t)r * 0x9E3779B97F4A7C15ull;
+    pyro_batch_ctx *b = new (std::nothrow) pyro_batch_ctx();
+    if (!b) return fail(PYRO_E_NOMEM, "host allocation failed");
+    const int rc = create(b->e, R, L, beta, model, precision, start, 1.0, seeds.data(), nullptr, nullptr);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return PYRO_OK;
+}
+
+int pyro_batch_sweep(pyro_batch b, int n)
+{
+    if (!b) return fail(PYRO_E_INVAL, "NULL handle");
+    if (n < 0) return fail(PYRO_E_INVAL, "n must be >= 0");
+    PYRO_CUDA(b->e.sweeps(n), "sweep launch");
+    return PYRO_OK;
+}
+
+int pyro_batch_stats(pyro_batch b, int r, pyro_stats_t *s)
+{
+    if (!b || !s || r < 0 || r >= b->e.R) return fail(PYRO_E_INVAL, "bad argument");
+    return stats_of(b->e, r, s);
+}
+
+int pyro_batch_reset_stats(pyro_batch b)
+{
+    if (!b) return fail(PYRO_E_INVAL, "NULL handle");
+    return reset_stats(b->e);
+}
+
+int pyro_batch_measure(pyro_batch b, int r, double *E, double *m2, double *m4)
+{
+    if (!b || r < 0 || r >= b->e.R) return fail(PYRO_E_INVAL, "bad argument");
+    return measure_of(b->e, r, E, m2, m4);
+}
+
+int pyro_batch_get_spins(pyro_batch b, int r, void *host, size_t bytes)
+{
+    if (!b || !host || r < 0 || r >= b->e.R) return fail(PYRO_E_INVAL, "bad argument");
+    return get_spins(b->e, r, host, bytes);
+}
+
+int pyro_batch_sync(pyro_batch b)
+{
+    if (!b) return fail(PYRO_E_INVAL, "NULL handle");
+    return finish(b->e);
+}
+
+int64_t pyro_batch_total_sites(pyro_batch b)
+{
+    if (!b) return 0;
+    int64_t n = 0;
+    for (const auto &r : b->e.reps) n += r.N;
+    return n;
+}
+
+uint64_t pyro_batch_launch_count(pyro_batch b) { return b ? b->e.launches : 0; }
+
+void pyro_batch_destroy(pyro_batch b)
+{
+    if (!b) return;
+    b->e.release();
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,466 @@
+// engine.cu -- host side of a set of lattices updated together: device
+// memory, the replica table, the launch sequence of a sweep, CUDA graphs of
+// multi-sweep chunks, and the per-replica measurement / accumulation kernel.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "engine.h"
+
+namespace pyro {
+
+// ising.cu
+size_t ising_local_smem(const TileShape &t);
+cudaError_t ising_prepare(const TileShape &t);
+void ising_launch_init(const Batch &B, int64_t nblocks, int random, cudaStream_t s);
+void ising_launch_phase(int p, const Batch &B, int64_t ntiles, int64_t nblocks, cudaStream_t s);
+void ising_launch_measure(const Batch &B, int64_t nblocks, cudaStream_t s);
+// vector.cu
+size_t vec_local_smem(const TileShape &t, int prec);
+cudaError_t vec_prepare(int model, int prec, const TileShape &t);
+void vec_launch_init(int model, int prec, const Batch &B, int64_t nblocks, int random, cudaStream_t s);
+void vec_launch_phase(int p, int model, int prec, const Batch &B, int64_t ntiles, int64_t nblocks, cudaStream_t s);
+void vec_launch_measure(int model, int prec, const Batch &B, int64_t nblocks, cudaStream_t s);
+
+// Per replica (one block each): reduce the per-block partials of the
+// measurement kernel in a fixed order, form E, m = |M|/N, m^2, m^4 (Eq. 1,
+// Eq. 2) and, in mode 1, add them to the Neumaier sums, append the trace
+// record and advance the sweep counter; mode 2 only records them as the last
+// measurement.
+template <bool ISING>
+__global__ void __launch_bounds__(1024) accumulate_kernel(const __grid_constant__ Batch B, int mode, int nc)
+{
+    const int r = blockIdx.x;
+    const Rep &R = B.reps[r];
+    DevStats *st = R.st;
+    const int64_t b0 = B.block_begin[r], b1 = B.block_begin[r + 1];
+    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+    if (ISING) {
+        __shared__ unsigned long long su[2][1024];
+        unsigned long long a = 0, d = 0;
+        for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+            const unsigned long long *p = reinterpret_cast<const unsigned long long *>(B.partials + 4 * b);
+            a += p[0];
+            d += p[1];
+        }
+        su[0][threadIdx.x] = a;
+        su[1][threadIdx.x] = d;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) {
+                su[0][threadIdx.x] += su[0][threadIdx.x + o];
+                su[1][threadIdx.x] += su[1][threadIdx.x + o];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x != 0) return;
+        const long long anti = (long long)su[0][0];
+        const long long M = R.N - 2 * (long long)su[1][0];
+        tot[0] = (double)(3 * R.N - 2 * anti);  // sum over bonds of s_i s_j
+        tot[1] = (double)M;
+    } else {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = __dadd_rn(v[q], B.partials[4 * b + q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tot[q] = block_sum_f64(v[q]);
+        if (threadIdx.x != 0) return;
+    }
+    const double E = __dmul_rn(-R.J, tot[0]);
+    double m;
+    if (ISING) {
+        m = __ddiv_rn(fabs(tot[1]), (double)R.N);
+    } else {
+        double msq = __dmul_rn(tot[1], tot[1]);
+        for (int k = 1; k < nc; ++k) msq = __dadd_rn(msq, __dmul_rn(tot[1 + k], tot[1 + k]));
+        m = __ddiv_rn(__dsqrt_rn(msq), (double)R.N);
+    }
+    const double m2 = __dmul_rn(m, m);
+    const double m4 = __dmul_rn(m2, m2);
+    st->last[0] = E;
+    st->last[1] = m2;
+    st->last[2] = m4;
+    st->last[3] = tot[1];
+    if (mode != 1) return;
+    nsum_add(st->acc_s[0], st->acc_c[0], E);
+    nsum_add(st->acc_s[1], st->acc_c[1], __dmul_rn(E, E));
+    nsum_add(st->acc_s[2], st->acc_c[2], m2);
+    nsum_add(st->acc_s[3], st->acc_c[3], m4);
+    nsum_add(st->acc_s[4], st->acc_c[4], __dsqrt_rn(m2));
+    if (R.trace && R.trace_cap > 0) {
+        double *rec = R.trace + 4 * (int64_t)(st->count % (unsigned long long)R.trace_cap);
+        rec[0] = E;
+        rec[1] = m2;
+        rec[2] = m4;
+        rec[3] = tot[1];
+    }
+    st->count += 1;
+    st->sweep += 1;
+}
+
+__global__ void set_params_kernel(Rep *reps, int r, uint64_t thr, double K2)
+{
+    reps[r].thr = thr;
+    reps[r].K2 = K2;
+}
+
+__global__ void set_trace_kernel(Rep *reps, int r, double *trace, int64_t cap)
+{
+    reps[r].trace = trace;
+    reps[r].trace_cap = cap;
+}
+
+__global__ void set_sweep_kernel(const __grid_constant__ Batch B, unsigned long long sweep)
+{
+    if ((int)threadIdx.x < B.R) B.reps[threadIdx.x].st->sweep = sweep;
+}
+
+// ------------------------------------------------------------------ host --
+uint64_t ising_threshold(double beta, double J)
+{
+    if (!(beta > 0.0)) return 0;
+    const double p = -expm1(-2.0 * beta * J);
+    if (!(p > 0.0)) return 0;
+    const double tq = floor(p * 4294967296.0);
+    return tq >= 4294967296.0 ? (1ull << 32) : (uint64_t)tq;
+}
+
+static int divisor_at_most(int L, int cap)
+{
+    for (int d = cap; d >= 1; --d)
+        if (L % d == 0) return d;
+    return 1;
+}
+
+TileShape default_tile(const int *Ls, int R, int model)
+{
+    int g = Ls[0];
+    for (int r = 1; r < R; ++r) {
+        int a = g, b = Ls[r];
+        while (b) {
+            const int t = a % b;
+            a = b;
+            b = t;
+        }
+        g = a;
+    }
+    if (model == PYRO_ISING) return TileShape{divisor_at_most(g, 8), divisor_at_most(g, 8), divisor_at_most(g, 4)};
+    return TileShape{divisor_at_most(g, 8), divisor_at_most(g, 4), divisor_at_most(g, 4)};
+}
+
+size_t local_smem(int model, int prec, const TileShape &t)
+{
+    return model == PYRO_ISING ? ising_local_smem(t) : vec_local_smem(t, prec);
+}
+
+std::string check_tile(const int *Ls, int R, int model, int prec, const TileShape &t)
+{
+    if (t.TX < 1 || t.TY < 1 || t.TZ < 1) return "tile edges must be positive";
+    for (int r = 0; r < R; ++r)
+        if (Ls[r] % t.TX || Ls[r] % t.TY || Ls[r] % t.TZ) return "tile edges must divide every L";
+    const int nt = t.TX * t.TY * t.TZ;
+    if (nt > (model == PYRO_ISING ? 1024 : 512)) return "tile has too many cells";
+    if (local_smem(model, prec, t) > 200 * 1024) return "tile needs too much shared memory";
+    return "";
+}
+
+static size_t spin_bytes_of(int model, int prec, int64_t N)
+{
+    if (model == PYRO_ISING) return (size_t)(N / 16) * sizeof(uint16_t);
+    return (size_t)N * model * (prec == PYRO_FP64 ? 8 : 4);
+}
+
+size_t Engine::spin_bytes(int r) const { return spin_bytes_of(model, prec, reps[r].N); }
+
+cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_, int prec_, int start_, double J,
+                          const uint64_t *seeds, cudaStream_t user_stream, const TileShape &t, std::string &err)
+{
+    R = R_;
+    model = model_;
+    prec = model_ == PYRO_ISING ? PYRO_FP64 : prec_;
+    start = start_;
+    tile = t;
+    cudaError_t e = cudaSuccess;
+    if (user_stream) {
+        stream = user_stream;
+        own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            err = "stream create";
+            return e;
+        }
+        own_stream = true;
+    }
+    std::memset(&B, 0, sizeof(B));
+    B.R = R;
+    B.TX = t.TX;
+    B.TY = t.TY;
+    B.TZ = t.TZ;
+    reps.assign(R, Rep{});
+    ntiles = 0;
+    nblocks = 0;
+    const int nt = t.TX * t.TY * t.TZ;
+    for (int r = 0; r < R; ++r) {
+        Rep &p = reps[r];
+        p.L = Ls[r];
+        p.ncells = (int64_t)Ls[r] * Ls[r] * Ls[r];
+        p.N = 16 * p.ncells;
+        p.ntx = Ls[r] / t.TX;
+        p.nty = Ls[r] / t.TY;
+        p.seed = seeds[r];
+        p.J = J;
+        p.thr = ising_threshold(betas ? betas[r] : 0.0, J);
+        p.K2 = 2.0 * (betas ? betas[r] : 0.0) * J;
+        beta.push_back(betas ? betas[r] : 0.0);
+        B.tile_begin[r] = ntiles;
+        B.block_begin[r] = nblocks;
+        ntiles += p.ncells / nt;
+        nblocks += (p.ncells + CELL_BLOCK - 1) / CELL_BLOCK;
+        struct {
+            void **ptr;
+            size_t bytes;
+        } al[] = {{&p.spins, spin_bytes_of(model, prec, p.N)},
+                  {(void **)&p.P, (size_t)p.N * sizeof(int32_t)},
+                  {(void **)&p.F, (size_t)p.ncells * sizeof(uint16_t)},
+                  {(void **)&p.dmask, (size_t)p.ncells * sizeof(uint32_t)},
+                  {(void **)&p.st, sizeof(DevStats)}};
+        for (auto &a : al) {
+            e = cudaMalloc(a.ptr, a.bytes);
+            if (e != cudaSuccess) {
+                err = "device allocation failed";
+                return e;
+            }
+            owned.push_back(*a.ptr);
+        }
+        e = cudaMemsetAsync(p.st, 0, sizeof(DevStats), stream);
+        if (e != cudaSuccess) return e;
+    }
+    B.tile_begin[R] = ntiles;
+    B.block_begin[R] = nblocks;
+    e = cudaMalloc(&B.partials, (size_t)nblocks * 4 * sizeof(double));
+    if (e != cudaSuccess) {
+        err = "device allocation failed";
+        return e;
+    }
+    owned.push_back(B.partials);
+    e = cudaMalloc(&d_reps, (size_t)R * sizeof(Rep));
+    if (e != cudaSuccess) {
+        err = "device allocation failed";
+        return e;
+    }
+    owned.push_back(d_reps);
+    B.reps = d_reps;
+    e = cudaMemcpyAsync(d_reps, reps.data(), (size_t)R * sizeof(Rep), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return e;
+    e = model == PYRO_ISING ? ising_prepare(tile) : vec_prepare(model, prec, tile);
+    if (e != cudaSuccess) {
+        err = "kernel attributes";
+        return e;
+    }
+    if (model == PYRO_ISING) ising_launch_init(B, nblocks, start == PYRO_START_RANDOM, stream);
+    else vec_launch_init(model, prec, B, nblocks, start == PYRO_START_RANDOM, stream);
+    launches += 1;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) err = "initial state";
+    return e;
+}
+
+void Engine::release()
+{
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto &g : graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+    for (void *p : owned) cudaFree(p);
+    owned.clear();
+    for (auto &r : reps)
+        if (r.trace) cudaFree(r.trace);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+}
+
+cudaError_t Engine::set_beta(int r, double b)
+{
+    if (beta[r] == b) return cudaSuccess;
+    beta[r] = b;
+    reps[r].thr = ising_threshold(b, reps[r].J);
+    reps[r].K2 = 2.0 * b * reps[r].J;
+    set_params_kernel<<<1, 1, 0, stream>>>(d_reps, r, reps[r].thr, reps[r].K2);
+    launches += 1;
+    return cudaGetLastError();
+}
+
+// Phase p of a sweep: 0 local labelling, 1 boundary unions, 2 flip,
+// 3 measurement, 4 accumulation (mode as in accumulate_kernel).
+void Engine::enqueue_phase(int p, int mode)
+{
+    if (p < 3) {
+        if (model == PYRO_ISING) ising_launch_phase(p, B, ntiles, nblocks, stream);
+        else vec_launch_phase(p, model, prec, B, ntiles, nblocks, stream);
+    } else if (p == 3) {
+        if (model == PYRO_ISING) ising_launch_measure(B, nblocks, stream);
+        else vec_launch_measure(model, prec, B, nblocks, stream);
+    } else {
+        if (model == PYRO_ISING) accumulate_kernel<true><<<R, 1024, 0, stream>>>(B, mode, 1);
+        else accumulate_kernel<false><<<R, 1024, 0, stream>>>(B, mode, model);
+    }
+}
+
+void Engine::enqueue_sweeps(int n)
+{
+    for (int s = 0; s < n; ++s)
+        for (int p = 0; p < NPHASE; ++p) enqueue_phase(p, 1);
+}
+
+void Engine::enqueue_measure(int mode)
+{
+    enqueue_phase(3, mode);
+    enqueue_phase(4, mode);
+}
+
+cudaError_t Engine::profile(int n, double *phase_ms)
+{
+    cudaEvent_t ev[NPHASE + 1];
+    for (auto &x : ev)
+        if (cudaEventCreate(&x) != cudaSuccess) return cudaGetLastError();
+    double acc[NPHASE] = {0, 0, 0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < n && e == cudaSuccess; ++s) {
+        cudaEventRecord(ev[0], stream);
+        for (int p = 0; p < NPHASE; ++p) {
+            enqueue_phase(p, 1);
+            cudaEventRecord(ev[p + 1], stream);
+        }
+        launches += NPHASE;
+        e = cudaEventSynchronize(ev[NPHASE]);
+        for (int p = 0; p < NPHASE && e == cudaSuccess; ++p) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[p], ev[p + 1]);
+            acc[p] += ms;
+        }
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    sweep += n;
+    labels_valid = true;
+    for (int p = 0; p < NPHASE; ++p) phase_ms[p] = n > 0 ? acc[p] / n : 0.0;
+    return e;
+}
+
+int Engine::launches_per_sweep() const { return NPHASE; }
+
+cudaGraphExec_t Engine::graph_for(int n)
+{
+    for (auto &g : graphs)
+        if (g.n == n) return g.exec;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    enqueue_sweeps(n);
+    if (cudaStreamEndCapture(stream, &graph) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    graphs.push_back(GraphEntry{n, exec});
+    return exec;
+}
+
+cudaError_t Engine::sweeps(int n)
+{
+    if (n <= 0) return cudaSuccess;
+    if (use_graphs && own_stream) {
+        const int chunk = n >= GRAPH_CHUNK ? GRAPH_CHUNK : 1;
+        cudaGraphExec_t gk = graph_for(chunk);
+        cudaGraphExec_t g1 = chunk == 1 ? gk : graph_for(1);
+        if (gk && g1) {
+            int left = n;
+            while (left >= chunk) {
+                const cudaError_t e = cudaGraphLaunch(gk, stream);
+                if (e != cudaSuccess) return e;
+                left -= chunk;
+                launches += (uint64_t)chunk * launches_per_sweep();
+            }
+            while (left > 0) {
+                const cudaError_t e = cudaGraphLaunch(g1, stream);
+                if (e != cudaSuccess) return e;
+                left -= 1;
+                launches += launches_per_sweep();
+            }
+            sweep += n;
+            labels_valid = true;
+            return cudaSuccess;
+        }
+    }
+    enqueue_sweeps(n);
+    launches += (uint64_t)n * launches_per_sweep();
+    sweep += n;
+    labels_valid = true;
+    return cudaGetLastError();
+}
+
+cudaError_t Engine::measure()
+{
+    enqueue_measure(2);
+    launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t Engine::set_sweep(uint64_t s)
+{
+    set_sweep_kernel<<<1, MAX_REPS, 0, stream>>>(B, s);
+    launches += 1;
+    sweep = s;
+    return cudaGetLastError();
+}
+
+cudaError_t Engine::set_trace(int r, int64_t cap)
+{
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return e;
+    if (reps[r].trace) cudaFree(reps[r].trace);
+    reps[r].trace = nullptr;
+    reps[r].trace_cap = 0;
+    if (cap > 0) {
+        e = cudaMalloc(&reps[r].trace, (size_t)cap * 4 * sizeof(double));
+        if (e != cudaSuccess) return e;
+        reps[r].trace_cap = cap;
+    }
+    set_trace_kernel<<<1, 1, 0, stream>>>(d_reps, r, reps[r].trace, reps[r].trace_cap);
+    launches += 1;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return e;
+}
+
+int Engine::read_status(std::string &err)
+{
+    int st = 0;
+    for (int r = 0; r < R; ++r) {
+        int s = 0;
+        cudaError_t e = cudaMemcpyAsync(&s, &reps[r].st->status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+        if (e != cudaSuccess) {
+            err = cudaGetErrorString(e);
+            return -1;
+        }
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            err = cudaGetErrorString(e);
+            return -1;
+        }
+        st |= s;
+    }
+    return st;
+}
+
+}  // namespace pyro

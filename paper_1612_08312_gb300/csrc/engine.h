@@ -1,0 +1,71 @@
+// engine.h -- host-side engine of one or more lattices updated together.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "ccl.cuh"
+
+namespace pyro {
+
+// Sweeps captured per CUDA graph for long runs.
+constexpr int GRAPH_CHUNK = 32;
+// Kernel launches (phases) per sweep: local labelling, boundary unions,
+// flip, measurement, accumulation.
+constexpr int NPHASE = 5;
+
+struct GraphEntry {
+    int n;
+    cudaGraphExec_t exec;
+};
+
+struct Engine {
+    int R = 0, model = 0, prec = 0, start = 0;
+    TileShape tile{1, 1, 1};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool use_graphs = true;
+    std::vector<Rep> reps;      // host copy of the replica table
+    std::vector<double> beta;   // current inverse temperature per replica
+    Rep *d_reps = nullptr;
+    Batch B;
+    int64_t ntiles = 0, nblocks = 0;
+    std::vector<void *> owned;
+    std::vector<GraphEntry> graphs;
+    uint64_t sweep = 0;
+    uint64_t launches = 0;
+    bool labels_valid = false;
+
+    cudaError_t setup(int R, const int *Ls, const double *betas, int model, int prec, int start, double J,
+                      const uint64_t *seeds, cudaStream_t user_stream, const TileShape &t, std::string &err);
+    void release();
+    size_t spin_bytes(int r) const;
+    cudaError_t set_beta(int r, double beta);
+    cudaError_t sweeps(int n);
+    cudaError_t measure();
+    cudaError_t set_sweep(uint64_t s);
+    cudaError_t set_trace(int r, int64_t cap);
+    int read_status(std::string &err);
+    int launches_per_sweep() const;
+
+    cudaError_t profile(int n, double *phase_ms);
+    void enqueue_phase(int p, int mode);
+    void enqueue_sweeps(int n);
+    void enqueue_measure(int mode);
+    cudaGraphExec_t graph_for(int n);
+};
+
+uint64_t ising_threshold(double beta, double J);
+TileShape default_tile(const int *Ls, int R, int model);
+std::string check_tile(const int *Ls, int R, int model, int prec, const TileShape &t);
+size_t local_smem(int model, int prec, const TileShape &t);
+
+}  // namespace pyro
+
+struct pyro_ctx {
+    pyro::Engine e;
+};
+
+struct pyro_batch_ctx {
+    pyro::Engine e;
+};

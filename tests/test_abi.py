@@ -1,0 +1,82 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+that include/pyro.h declares; the Python binding covers the same names.
+Argument checks that run before any CUDA call are exercised on the CPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1612_08312_gb300 as pyro
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(pyro_[a-z_0-9]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for core in ("pyro_init", "pyro_sweep", "pyro_measure"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = pyro._build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (pyro_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_binding_uses_the_c_names():
+    assert sorted(pyro.declared_symbols()) == declared_functions()
+    for n in declared_functions():
+        assert callable(getattr(pyro, n))
+
+
+def test_build_targets_sm_103a_only():
+    assert pyro._build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.parametrize("L,model", [(0, 1), (512, 1), (4, 0), (4, 4), (-3, 2)])
+def test_init_rejects_bad_arguments(L, model):
+    with pytest.raises(pyro.PyroError) as ei:
+        pyro.pyro_init_ex(L, model, 1)
+    assert ei.value.code == pyro.E_INVAL
+
+
+def test_init_rejects_bad_tile_and_options():
+    for kw in (dict(tile=(3, 8, 4)), dict(tile=(8, 8, 32)), dict(precision=7), dict(start=5), dict(J=0.0),
+               dict(J=float("nan"))):
+        with pytest.raises(pyro.PyroError) as ei:
+            pyro.pyro_init_ex(8, pyro.ISING, 1, **kw)
+        assert ei.value.code == pyro.E_INVAL
+
+
+def test_null_handle_calls_fail_cleanly():
+    L = pyro.lib()
+    assert L.pyro_sweep(None, 0.2, 1) == pyro.E_INVAL
+    assert L.pyro_sync(None) == pyro.E_INVAL
+    assert L.pyro_measure(None, None, None, None) == pyro.E_INVAL
+    assert L.pyro_num_sites(None) == 0
+    assert "NULL" in pyro.pyro_last_error()
+    L.pyro_destroy(None)
+
+
+def test_batch_rejects_bad_arguments():
+    for Ls, betas in (([8] * 65, [0.2] * 65), ([8, 0], [0.2, 0.2]), ([8], [-1.0]), ([8], [float("inf")])):
+        with pytest.raises(pyro.PyroError) as ei:
+            pyro.pyro_batch_init(Ls, betas, pyro.ISING)
+        assert ei.value.code == pyro.E_INVAL

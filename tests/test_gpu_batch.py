@@ -1,0 +1,57 @@
+"""Batched replicas: every phase of a sweep is one launch over all replicas'
+tiles and long runs replay captured CUDA graphs; each replica must still be
+exactly the chain of a single lattice with the replica's seed (and so the
+oracle's chain)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1612_08312_gb300 as pyro
+
+pytestmark = pytest.mark.gpu
+
+
+def test_ising_batch_matches_single_lattices_and_oracle():
+    Ls = [4, 8, 8, 12, 16]
+    Ts = [4.19, 4.21, 4.22, 4.23, 4.24]
+    b = pyro.Replicas(Ls, [1 / T for T in Ts], pyro.ISING, start="random", seed=1)
+    b.sweep(37)
+    for r, (L, T) in enumerate(zip(Ls, Ts)):
+        seed = pyro.replica_seed(1, r)
+        o = oracle.Oracle(L, oracle.ISING, seed, "random")
+        o.sweep(1 / T, 37)
+        assert (b.spins(r) == o.spins()).all(), r
+        assert b.stats(r) == o.stats(), r
+        assert b.measure(r) == o.measure(), r
+
+
+@pytest.mark.parametrize("model", [2, 3])
+def test_vector_fp64_batch_matches_oracle(model):
+    Ls = [2, 4, 4]
+    Ts = [1.2, 1.3, 2.0]
+    b = pyro.Replicas(Ls, [1 / T for T in Ts], model, precision=pyro.FP64, start="random", seed=5)
+    b.sweep(3)
+    for r, (L, T) in enumerate(zip(Ls, Ts)):
+        o = oracle.Oracle(L, model, pyro.replica_seed(5, r), "random")
+        o.sweep(1 / T, 3)
+        assert np.abs(b.spins(r) - o.spins()).max() < 1e-12
+
+
+def test_batch_graph_chunks_and_launch_accounting():
+    b = pyro.Replicas([8, 8], [0.23, 0.24], pyro.ISING, start="random", seed=9)
+    l0 = b.launches
+    b.sweep(70)  # two 32-sweep graphs plus six single-sweep graphs
+    b.sync()
+    assert b.launches - l0 == 70 * 5
+    s = b.stats(0)
+    assert s["count"] == 70
+
+
+def test_mixed_sizes_uneven_tiles():
+    Ls = [16, 24, 32]
+    b = pyro.Replicas(Ls, [1 / 4.21394] * 3, pyro.ISING, start="random", seed=2)
+    b.sweep(5)
+    for r, L in enumerate(Ls):
+        o = oracle.Oracle(L, oracle.ISING, pyro.replica_seed(2, r), "random")
+        o.sweep(1 / 4.21394, 5)
+        assert (b.spins(r) == o.spins()).all()

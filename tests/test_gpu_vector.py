@@ -1,0 +1,124 @@
+"""XY and Heisenberg parity (Wolff embedded clusters, Sec. 2).
+
+FP64: from the same configuration and random stream, one sweep must give the
+oracle's labels exactly and its spins and energy to 1e-12.  The FP64 kernels
+use correctly rounded operations in the oracle's order, so a difference can
+only come from a bond whose uniform lies within an ulp of its probability
+(libm and CUDA expm1 may round differently); the test asserts there is none.
+
+FP32: spins stored and updated in float against the FP64 oracle, from an
+FP32-representable start.  A bond decision may differ only where the
+uniform lies within 2^-20 of the FP64 probability (a near tie); when no
+decision differs the energy after one sweep must agree to 1e-6 relative."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1612_08312_gb300 as pyro
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def fp64_pair(model, L, T, seed, sweeps, start="random", tile=(0, 0, 0)):
+    o = oracle.Oracle(L, model, seed, start)
+    g = pyro.Lattice(L, model, seed, precision=pyro.FP64, start=start, tile=tile)
+    assert np.abs(g.spins() - o.spins()).max() == 0.0  # same initial state, bit for bit
+    for s in range(sweeps):
+        o.sweep(1 / T, 1)
+        g.sweep(1 / T, 1)
+        assert (g.labels() == o.labels()).all(), f"labels differ after sweep {s}"
+        assert np.abs(g.spins() - o.spins()).max() <= 1e-12
+        Eg, m2g, m4g = g.measure()
+        Eo, m2o, m4o = o.measure()
+        assert abs(Eg - Eo) <= 1e-12 * abs(Eo) + 1e-12
+        assert abs(m2g - m2o) <= 1e-12 * m2o + 1e-15 and abs(m4g - m4o) <= 1e-12 * m4o + 1e-15
+    return o, g
+
+
+@pytest.mark.parametrize("model", [2, 3])
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 8])
+def test_fp64_every_sweep(model, L):
+    T = workloads.TC[model]
+    fp64_pair(model, L, T, seed=13 + L, sweeps=5)
+
+
+@pytest.mark.parametrize("model", [2, 3])
+@pytest.mark.parametrize("tile", [(1, 1, 1), (2, 2, 2), (4, 4, 4), (8, 4, 2)])
+def test_fp64_tiles(model, tile):
+    fp64_pair(model, 8, workloads.TC[model], seed=3, sweeps=3, tile=tile)
+
+
+@pytest.mark.parametrize("model", [2, 3])
+def test_fp64_ordered_start_and_limits(model):
+    o, g = fp64_pair(model, 4, 1e-3, seed=5, sweeps=2, start="up")  # beta = 1000: one cluster
+    assert (g.labels() == 0).all()
+    E, m2, m4 = g.measure()
+    assert abs(E + 3 * g.N) < 1e-9 * g.N
+    h = pyro.Lattice(4, model, 5, precision=pyro.FP64, start="random")
+    h.sweep(0.0, 1)  # beta = 0: no bond is active
+    assert (h.labels() == np.arange(h.N)).all()
+
+
+@pytest.mark.parametrize("model", [2, 3])
+def test_fp64_accumulators(model):
+    o, g = fp64_pair(model, 4, workloads.TC[model], seed=17, sweeps=1)
+    o.sweep(1 / workloads.TC[model], 30)
+    g.sweep(1 / workloads.TC[model], 30)
+    so, sg = o.stats(), g.stats()
+    assert sg["count"] == so["count"] == 31
+    for k in ("sum_E", "sum_E2", "sum_m2", "sum_m4", "sum_absm"):
+        assert abs(sg[k] - so[k]) <= 1e-11 * abs(so[k]) + 1e-14, k
+
+
+def near_ties(model, L, T, seed, s0, sweep_index):
+    """Bonds of one sweep whose uniform lies within 2^-20 of the FP64
+    probability, recomputed from the oracle's configuration."""
+    o = oracle.Oracle(L, model, seed, "up")
+    o.set_spins(s0)
+    o.sweep_count = sweep_index
+    o.sweep(1 / T, 1)
+    r = o.axis()
+    bi, bj = o.bonds()
+    proj = s0 @ r
+    x = proj[bi] * proj[bj]
+    idx = np.nonzero(x > 0)[0]
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    ties = 0
+    for b in idx.tolist():
+        w = oracle.philox([(b >> 2) & 0xFFFFFFFF, b >> 34, sweep_index, 1], key)[b & 3]
+        u = (float(w) + 0.5) / 2 ** 32
+        p = -math.expm1(-2 / T * x[b])
+        ties += abs(u - p) < 2 ** -20
+    return o, ties
+
+
+@pytest.mark.parametrize("model", [2, 3])
+@pytest.mark.parametrize("L", [2, 4, 8, 16])
+def test_fp32_single_sweep_energy(model, L):
+    T = workloads.TC[model]
+    seed = 29 + L
+    s0 = workloads.random_unit_vectors(16 * L ** 3, model, seed=L, fp32_exact=True)
+    g = pyro.Lattice(L, model, seed, precision=pyro.FP32, start="up")
+    g.set_spins(s0)
+    assert (g.spins() == s0).all()
+    g.sweep(1 / T, 1)
+    o, ties = near_ties(model, L, T, seed, s0, 0)
+    same_clusters = (g.labels() == o.labels()).all()
+    if not same_clusters:
+        assert ties > 0, "FP32 bond decisions differ without a near tie"
+        pytest.skip(f"{ties} near-tie bond(s): FP32 and FP64 clusters legitimately differ")
+    Eg, _, _ = g.measure()
+    Eo, _, _ = o.measure()
+    assert abs(Eg - Eo) <= 1e-6 * abs(Eo)
+    assert np.abs(g.spins() - o.spins()).max() < 1e-5
+    assert np.allclose(np.linalg.norm(g.spins(), axis=1), 1.0, atol=1e-6)
+
+
+@pytest.mark.parametrize("model", [2, 3])
+def test_fp32_random_start_is_rounded_fp64_start(model):
+    o = oracle.Oracle(4, model, 77, "random")
+    g = pyro.Lattice(4, model, 77, precision=pyro.FP32, start="random")
+    assert (g.spins() == o.spins().astype(np.float32).astype(np.float64)).all()
