@@ -60,6 +60,8 @@ def lib():
                 getattr(L, name).argtypes = [c.c_void_p, c.c_void_p]
             L.orc_get_bonds.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p]
             L.orc_philox.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p]
+            L.orc_bond_word.restype = c.c_uint32
+            L.orc_bond_word.argtypes = [c.c_uint64, c.c_uint32, c.c_uint64]
             L.orc_threshold.restype = c.c_uint64
             L.orc_threshold.argtypes = [c.c_double, c.c_double]
             L.orc_unit_vector.restype = c.c_int
@@ -86,6 +88,11 @@ def philox(counter, key) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib().orc_philox(_ptr(c), _ptr(k), _ptr(out))
     return out
+
+
+def bond_word(seed: int, sweep: int, b: int) -> int:
+    """The 32-bit uniform of bond b in sweep `sweep`."""
+    return int(lib().orc_bond_word(seed, sweep, b))
 
 
 def threshold(beta: float, J: float = 1.0) -> int:

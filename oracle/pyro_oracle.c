@@ -21,8 +21,13 @@
  *   - bond id b = 12*r + k, r = i >> 2 the FCC point, k = 0..5 the pairs of
  *     the "up" tetrahedron of r, k = 6..11 the pairs of the "down"
  *     tetrahedron whose basis-0 vertex is site 4r;
- *   - random words from Philox4x32-10 keyed by the seed, counter
- *     (j_lo, j_hi, sweep, tag);
+ *   - random numbers from Philox4x32-10 keyed by the seed, counter
+ *     (j_lo, j_hi, sweep, tag).  A call yields 128 bits, read as eight
+ *     16-bit halves (half h = bits 16 (h & 1) .. of output word h >> 1) or
+ *     as 128 single bits (bit t = bit t & 31 of output word t >> 5);
+ *   - bond b's 32-bit uniform w_b: high half = half (b & 7) of BOND call
+ *     b >> 3, low half = half (b & 7) of TIE call b >> 3;
+ *   - one flip bit per cluster: bit (root & 127) of FLIP call root >> 7;
  *   - canonical cluster label = minimum site index of the cluster.
  *
  * The nearest-neighbour table is found GEOMETRICALLY (every lattice point at
@@ -43,6 +48,7 @@
 #define TAG_FLIP 2u
 #define TAG_AXIS 3u
 #define TAG_INIT 4u
+#define TAG_TIE 5u
 #define INIT_SWEEP_FIELD 0xFFFFFFFFu
 #define MAX_AXIS_ATTEMPTS 256
 
@@ -74,29 +80,52 @@ void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Word x of the stream (seed, sweep field, tag): output word x & 3 of the
- * Philox call with call index j = x >> 2. */
-static uint32_t stream_word(uint64_t seed, uint32_t sweep_field, uint32_t tag, uint64_t x)
+static void stream_call(uint64_t seed, uint32_t sweep_field, uint32_t tag, uint64_t j, uint32_t out[4])
 {
-    uint64_t j = x >> 2;
     uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(j >> 32), sweep_field, tag};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t out[4];
     orc_philox(ctr, key, out);
-    return out[x & 3];
 }
 
-/* Ising bond threshold: a satisfied bond is active iff its word w < T_beta,
- * T_beta = floor(p * 2^32), p = 1 - exp(-2 beta J) (Swendsen-Wang bond
- * probability; SW87 as cited in Sec. 1).  Returned in 64 bits so that p = 1
- * gives 2^32 (every word below it). */
-uint64_t orc_threshold(double beta, double J)
+/* Half x of the stream (seed, sweep field, tag): 16-bit half x & 7 of the
+ * Philox call with call index x >> 3. */
+static uint32_t stream_half(uint64_t seed, uint32_t sweep_field, uint32_t tag, uint64_t x)
 {
-    double p = -expm1(-2.0 * beta * J);
+    uint32_t out[4];
+    stream_call(seed, sweep_field, tag, x >> 3, out);
+    return (out[(x & 7) >> 1] >> (16 * (x & 1))) & 0xFFFFu;
+}
+
+/* Bit x of the stream: bit x & 127 of the Philox call with index x >> 7. */
+static uint32_t stream_bit(uint64_t seed, uint32_t sweep_field, uint32_t tag, uint64_t x)
+{
+    uint32_t out[4];
+    stream_call(seed, sweep_field, tag, x >> 7, out);
+    return (out[(x & 127) >> 5] >> (x & 31)) & 1u;
+}
+
+/* The 32-bit uniform of bond b in a sweep. */
+uint32_t orc_bond_word(uint64_t seed, uint32_t sweep_field, uint64_t b)
+{
+    return (stream_half(seed, sweep_field, TAG_BOND, b) << 16) | stream_half(seed, sweep_field, TAG_TIE, b);
+}
+
+/* Threshold of a bond with activation probability p: the bond is active iff
+ * its uniform w < floor(p * 2^32).  Returned in 64 bits so that p = 1 gives
+ * 2^32 (every word below it). */
+static uint64_t prob_threshold(double p)
+{
     if (!(p > 0.0)) return 0;
     double t = floor(p * 4294967296.0);
     if (t >= 4294967296.0) return (uint64_t)1 << 32;
     return (uint64_t)t;
+}
+
+/* Ising: a satisfied bond is active with p = 1 - exp(-2 beta J)
+ * (Swendsen-Wang bond probability; SW87 as cited in Sec. 1). */
+uint64_t orc_threshold(double beta, double J)
+{
+    return prob_threshold(-expm1(-2.0 * beta * J));
 }
 
 /* Uniform random unit vector for the embedded-cluster axis (n = 2, 3) and
@@ -317,7 +346,7 @@ void orc_free(orc *h)
 }
 
 /* start: 0 = ordered (Ising all +1, continuous e_0), 1 = random.
- * Random Ising: sigma_i = +1 iff bit 31 of word i of the INIT stream is 0.
+ * Random Ising: sigma_i = -1 iff bit i of the INIT stream is 1.
  * Random continuous: site i draws orc_unit_vector with call_base = i << 8. */
 orc *orc_new(int L, int model, uint64_t seed, int start, double J)
 {
@@ -345,7 +374,7 @@ orc *orc_new(int L, int model, uint64_t seed, int start, double J)
     for (int64_t i = 0; i < h->N; ++i) h->label[i] = (int32_t)i;
     if (model == ORC_ISING) {
         for (int64_t i = 0; i < h->N; ++i) {
-            int neg = start ? (int)(stream_word(seed, INIT_SWEEP_FIELD, TAG_INIT, (uint64_t)i) >> 31) : 0;
+            int neg = start ? (int)stream_bit(seed, INIT_SWEEP_FIELD, TAG_INIT, (uint64_t)i) : 0;
             h->sigma[i] = neg ? -1 : 1;
         }
     } else {
@@ -408,7 +437,7 @@ static void sweep_once(orc *h, double beta, double *trace)
             int32_t i = h->bond_i[b], j = h->bond_j[b];
             int act = 0;
             if (h->sigma[i] == h->sigma[j]) {
-                uint32_t w = stream_word(h->seed, sw, TAG_BOND, (uint64_t)b);
+                uint32_t w = orc_bond_word(h->seed, sw, (uint64_t)b);
                 act = ((uint64_t)w < thr);
             }
             h->active[b] = (uint8_t)act;
@@ -426,9 +455,8 @@ static void sweep_once(orc *h, double beta, double *trace)
             int act = 0;
             if (x > 0.0) {
                 double prob = -expm1(-(K2 * x));
-                uint32_t w = stream_word(h->seed, sw, TAG_BOND, (uint64_t)b);
-                double u = ((double)w + 0.5) * (1.0 / 4294967296.0);
-                act = (u < prob);
+                uint32_t w = orc_bond_word(h->seed, sw, (uint64_t)b);
+                act = ((uint64_t)w < prob_threshold(prob));
             }
             h->active[b] = (uint8_t)act;
         }
@@ -439,8 +467,7 @@ static void sweep_once(orc *h, double beta, double *trace)
 
     /* 3-4. each cluster flips with probability 1/2, keyed by its root */
     for (int64_t i = 0; i < N; ++i) {
-        uint32_t fw = stream_word(h->seed, sw, TAG_FLIP, (uint64_t)h->label[i]);
-        if ((fw >> 31) == 0) continue;
+        if (!stream_bit(h->seed, sw, TAG_FLIP, (uint64_t)h->label[i])) continue;
         if (h->model == ORC_ISING) {
             h->sigma[i] = (int8_t)(-h->sigma[i]);
         } else {

@@ -172,15 +172,39 @@ def curand_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
     return out
 
 
-def stream_words(seed: int, sweep_field: int, tag: int, idx: np.ndarray) -> np.ndarray:
-    """Word x of a (seed, sweep, tag) stream via cuRAND: output word x & 3 of
-    the call with counter (x >> 2 low, x >> 2 high, sweep, tag)."""
-    idx = np.asarray(idx, dtype=np.uint64)
-    j = idx >> np.uint64(2)
+def _stream_calls(seed: int, sweep_field: int, tag: int, j: np.ndarray) -> np.ndarray:
+    j = np.asarray(j, dtype=np.uint64)
     ctr = np.stack([(j & np.uint64(0xFFFFFFFF)).astype(np.uint32),
                     (j >> np.uint64(32)).astype(np.uint32),
-                    np.full(len(idx), sweep_field, dtype=np.uint32),
-                    np.full(len(idx), tag, dtype=np.uint32)], 1)
-    key = np.tile(np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32), (len(idx), 1))
-    out = curand_philox(ctr, key)
-    return out[np.arange(len(idx)), (idx & np.uint64(3)).astype(np.int64)]
+                    np.full(len(j), sweep_field, dtype=np.uint32),
+                    np.full(len(j), tag, dtype=np.uint32)], 1)
+    key = np.tile(np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32), (len(j), 1))
+    return curand_philox(ctr, key)
+
+
+def stream_halves(seed: int, sweep_field: int, tag: int, idx: np.ndarray) -> np.ndarray:
+    """16-bit half x of a (seed, sweep, tag) stream via cuRAND: half x & 7
+    (bits 16 (h & 1) and up of output word h >> 1) of call x >> 3."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    out = _stream_calls(seed, sweep_field, tag, idx >> np.uint64(3))
+    h = (idx & np.uint64(7)).astype(np.int64)
+    w = out[np.arange(len(idx)), h >> 1]
+    return ((w >> (16 * (h & 1)).astype(np.uint32)) & np.uint32(0xFFFF)).astype(np.uint32)
+
+
+def stream_bits(seed: int, sweep_field: int, tag: int, idx: np.ndarray) -> np.ndarray:
+    """Bit x of a stream via cuRAND: bit x & 31 of output word (x & 127) >> 5
+    of call x >> 7."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    out = _stream_calls(seed, sweep_field, tag, idx >> np.uint64(7))
+    t = (idx & np.uint64(127)).astype(np.int64)
+    w = out[np.arange(len(idx)), t >> 5]
+    return ((w >> (t & 31).astype(np.uint32)) & np.uint32(1)).astype(np.uint32)
+
+
+def bond_words(seed: int, sweep: int, bonds: np.ndarray) -> np.ndarray:
+    """32-bit uniform of each bond: BOND-stream half as the high 16 bits,
+    TIE-stream half (tag 5) as the low 16 bits."""
+    hi = stream_halves(seed, sweep, 1, bonds).astype(np.uint64)
+    lo = stream_halves(seed, sweep, 5, bonds).astype(np.uint64)
+    return (hi << np.uint64(16)) | lo

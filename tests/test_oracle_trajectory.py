@@ -1,11 +1,12 @@
 """Second-implementation checks of one oracle sweep.
 
 A sweep is recomputed step by step in numpy from the spins before it, with
-random words from cuRAND's Philox (not the oracle's), clusters from
+random numbers from cuRAND's Philox (not the oracle's), clusters from
 scipy.sparse.csgraph, and the bond list from the geometry test's pinned
-tetrahedra.  This pins the index conventions (bond id, call index, word
-slot, tags, sweep field), the bond rule of each model, the canonical root,
-the flip and the reflection s -> s - 2 (s.r) r (Wolff embedding, Sec. 2)."""
+tetrahedra.  This pins the index conventions (bond id, call index, 16-bit
+half and single-bit slots, tags, sweep field), the bond rule of each model,
+the canonical root, the flip and the reflection s -> s - 2 (s.r) r (Wolff
+embedding, Sec. 2)."""
 import math
 
 import numpy as np
@@ -16,7 +17,7 @@ from scipy.sparse.csgraph import connected_components
 import oracle
 import refmath
 
-BOND, FLIP, AXIS = 1, 2, 3
+BOND, FLIP, AXIS, INIT, TIE = 1, 2, 3, 4, 5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -61,14 +62,14 @@ def test_ising_sweep_recomputed(L, T, seed):
         s0 = o.spins().astype(np.int64)
         o.sweep(beta, 1)
         sat = s0[bi] == s0[bj]
-        w = refmath.stream_words(seed, k, BOND, np.arange(3 * N))
+        w = refmath.bond_words(seed, k, np.arange(3 * N))
         thr = math.floor(-math.expm1(-2 * beta) * 2 ** 32)
         act = sat & (w.astype(np.int64) < thr)
         assert (o.active().astype(bool) == act).all()
         lab = min_index_labels(N, bi, bj, act)
         assert (o.labels() == lab).all()
-        fw = refmath.stream_words(seed, k, FLIP, lab)
-        s1 = np.where(fw >> 31 == 1, -s0, s0)
+        fb = refmath.stream_bits(seed, k, FLIP, lab)
+        s1 = np.where(fb == 1, -s0, s0)
         assert (o.spins() == s1).all()
         E, m2, m4 = o.measure()
         assert E == -float((s1[bi] * s1[bj]).sum())
@@ -78,8 +79,8 @@ def test_ising_sweep_recomputed(L, T, seed):
 
 def test_random_ising_start_recomputed():
     o = oracle.Oracle(2, oracle.ISING, seed=99, start="random")
-    w = refmath.stream_words(99, 0xFFFFFFFF, 4, np.arange(o.N))
-    assert (o.spins() == np.where(w >> 31 == 1, -1, 1)).all()
+    b = refmath.stream_bits(99, 0xFFFFFFFF, INIT, np.arange(o.N))
+    assert (o.spins() == np.where(b == 1, -1, 1)).all()
 
 
 @pytest.mark.parametrize("model", [2, 3])
@@ -99,18 +100,18 @@ def test_vector_sweep_recomputed(model, L, T):
         assert (o.axis() == r).all()
         proj = s0 @ r
         x = proj[bi] * proj[bj]
-        w = refmath.stream_words(seed, k, BOND, np.arange(3 * N)).astype(np.float64)
-        u = (w + 0.5) / 2 ** 32
+        w = refmath.bond_words(seed, k, np.arange(3 * N)).astype(np.float64)
         p = -np.expm1(-2 * beta * np.maximum(x, 0))
-        act = (x > 0) & (u < p)
-        # a decision within 1e-12 of the threshold may legitimately differ in
+        thr = np.floor(p * 2 ** 32)
+        act = (x > 0) & (w < thr)
+        # a threshold within 1e-4 of an integer may legitimately differ in
         # the last bit of p between numpy and libm; none are expected here
-        assert (np.abs(u - p)[x > 0] > 1e-12).all()
+        frac = p * 2 ** 32 - thr
+        assert (np.minimum(frac, 1 - frac)[x > 0] > 1e-4).all()
         assert (o.active().astype(bool) == act).all()
         lab = min_index_labels(N, bi, bj, act)
         assert (o.labels() == lab).all()
-        fw = refmath.stream_words(seed, k, FLIP, lab)
-        flip = (fw >> 31) == 1
+        flip = refmath.stream_bits(seed, k, FLIP, lab) == 1
         s1 = s0.copy()
         refl = s0 - 2 * proj[:, None] * r[None, :]
         refl /= np.linalg.norm(refl, axis=1, keepdims=True)
