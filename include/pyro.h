@@ -180,6 +180,47 @@ void pyro_destroy(pyro_handle h);
 /* Message of the last failed call on this thread ("" if none). */
 const char *pyro_last_error(void);
 
+/* ---- sweep without allocation ------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * must not allocate device memory: a sweep embedded in an application whose
+ * framework owns the device memory budget through its own caching
+ * allocator, a plugin that may not allocate after start-up, or a latency-
+ * sensitive loop in which cudaMalloc/cudaFree would synchronise the device
+ * and stall other streams.
+ *
+ * One Ising Swendsen-Wang sweep, the same chain step as pyro_sweep on a
+ * lattice with this seed and sweep counter (same conventions as above),
+ * with every input and output supplied by the caller and all scratch memory
+ * (flip bits, tile-crossing bond masks, per-block partial sums, the lattice
+ * record and its statistics) taken from one file-scope device array of
+ * PYRO_NOALLOC_SCRATCH_BYTES bytes.  That array exists on every GPU that
+ * loads the library and stays there until the process exits.
+ *
+ *   spins_in   device, L^3 uint16 in the compact layout of pyro_get_state
+ *   spins_out  device, L^3 uint16: the spins after the sweep (may equal
+ *              spins_in for an in-place update)
+ *   labels     device, 16 L^3 int32: canonical cluster labels of the sweep
+ *              (also used as the union-find workspace)
+ *   meas       device, 4 doubles: E, m^2, m^4 and M of the new configuration
+ *   L          1 <= L <= PYRO_NOALLOC_MAX_L, else PYRO_E_INVAL
+ *   beta, seed, sweep   inverse temperature (J = 1), Philox key, sweep field
+ *   stream     cudaStream_t to run on (NULL = the legacy default stream)
+ *
+ * Calls no cudaMalloc, cudaFree or other allocating routine.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture.  Every
+ * call on a device uses the same array, which keeps the previous call's
+ * contents; the call re-initialises what must start from zero.  Calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on the
+ * array and must be serialised by the caller.  Synchronises the stream
+ * before returning, and returns PYRO_E_NOCONVERGE if a union-find loop hit
+ * its bound. */
+#define PYRO_NOALLOC_MAX_L 64
+#define PYRO_NOALLOC_SCRATCH_BYTES 1606144
+int pyro_ising_sweep_noalloc(const uint16_t *spins_in, uint16_t *spins_out, int32_t *labels, double *meas,
+                             int L, double beta, uint64_t seed, uint64_t sweep, void *stream);
+
 /* ---- batched replicas ----------------------------------------------------- */
 
 /* R independent lattices of sizes L[r] at inverse temperatures beta[r],

@@ -87,6 +87,9 @@ _SIGS = {
     "pyro_batch_total_sites": (ctypes.c_int64, [ctypes.c_void_p]),
     "pyro_batch_launch_count": (ctypes.c_uint64, [ctypes.c_void_p]),
     "pyro_batch_destroy": (None, [ctypes.c_void_p]),
+    "pyro_ising_sweep_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
+                                                ctypes.c_void_p]),
 }
 
 
@@ -305,6 +308,16 @@ def pyro_batch_launch_count(b) -> int:
 
 def pyro_batch_destroy(b):
     lib().pyro_batch_destroy(b)
+
+
+NOALLOC_MAX_L = 64
+
+
+def pyro_ising_sweep_noalloc(spins_in: int, spins_out: int, labels: int, meas: int, L: int, beta: float,
+                             seed: int, sweep: int, stream: int | None = None):
+    """One Ising sweep on caller-owned device buffers (raw device pointers),
+    with the library's fixed scratch array instead of any allocation."""
+    _check(lib().pyro_ising_sweep_noalloc(spins_in, spins_out, labels, meas, L, beta, seed, sweep, stream))
 
 
 # ------------------------------------------------------- convenience API --

@@ -116,6 +116,13 @@ __global__ void set_sweep_kernel(const __grid_constant__ Batch B, unsigned long 
     if ((int)threadIdx.x < B.R) B.reps[threadIdx.x].st->sweep = sweep;
 }
 
+// Host launcher of the accumulation kernel for callers outside this file.
+void launch_accumulate(const Batch &B, bool ising, int mode, int nc, cudaStream_t s)
+{
+    if (ising) accumulate_kernel<true><<<B.R, 1024, 0, s>>>(B, mode, nc);
+    else accumulate_kernel<false><<<B.R, 1024, 0, s>>>(B, mode, nc);
+}
+
 // ------------------------------------------------------------------ host --
 uint64_t ising_threshold(double beta, double J)
 {
