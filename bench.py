@@ -37,16 +37,17 @@ FALLBACK_HBM_GBS = 6800.0
 # Algorithmic bytes per site of one sweep (bit-packed spins read + written,
 # one int32 label written and read): the whole-sweep HBM model.
 SWEEP_BYTES_PER_SITE = 8.25
-# Algorithmic bytes per site of each phase of the Ising sweep.
+# Bytes per site each phase of the Ising sweep must move in HBM.
 PHASE_BYTES_PER_SITE = {
-    "local": 0.125 + 4.0,      # spin words read, tile-local root labels written
-    "boundary": 0.0,           # only tile-crossing bonds; not credited
-    "flip": 4.0 + 0.25,        # labels read, spin words read and written
-    "measure": 0.125,          # spin words read
+    "local": 0.125 + 2.0 + 0.125,   # spin words read; 16-bit local labels and flip words written
+    "binit": 0.0,                   # only tile-crossing pairs; not credited
+    "bunite": 0.0,
+    "flip": 2.0 + 0.125 + 0.25,     # local labels and flip words read; spin words read and written
+    "measure": 0.125,               # spin words read
     "accumulate": 0.0,
 }
-KERNEL_NAMES = {"local": "ising_local_kernel", "boundary": "boundary_kernel", "flip": "ising_flip_kernel",
-                "measure": "ising_measure_kernel", "accumulate": "accumulate_kernel"}
+KERNEL_NAMES = {"local": "ising_local_kernel", "binit": "boundary_kernel<false>", "bunite": "boundary_kernel<true>",
+                "flip": "ising_flip_kernel", "measure": "ising_measure_kernel", "accumulate": "accumulate_kernel"}
 
 
 def peaks():

@@ -23,16 +23,21 @@
  *                (0,3) (1,2) (1,3) (2,3) of basis vertices of the tetrahedron
  *                of FCC point r, k = 6..11 the same pairs of the other
  *                tetrahedron through site 4r;
- *   random words Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
- *                (j_lo, j_hi, sweep, tag), word x = output x & 3 of call
- *                j = x >> 2; tags 1 bond, 2 flip, 3 axis, 4 initial state
- *                (sweep field 0xFFFFFFFF);
+ *   random bits  Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
+ *                (j_lo, j_hi, sweep, tag); tags 1 bond, 2 flip, 3 axis,
+ *                4 initial state (sweep field 0xFFFFFFFF), 5 tie.  A call's
+ *                128 bits are read as eight 16-bit halves (half h: bits
+ *                16 (h & 1).. of output word h >> 1) or as 128 bits (bit t:
+ *                bit t & 31 of output word t >> 5);
+ *   bond uniform w_b = (half b & 7 of bond call b >> 3) << 16 | (half b & 7
+ *                of tie call b >> 3); the tie half is only needed when the
+ *                high halves of w_b and the threshold are equal;
  *   Ising bond   active iff s_i = s_j and w_b < floor((1 - exp(-2 beta J))
  *                2^32);
  *   n-vector     axis r drawn once per sweep; active iff p_i p_j > 0 and
- *                (w_b + 1/2) 2^-32 < 1 - exp(-2 beta J p_i p_j), p_i = s_i.r;
+ *                w_b < floor((1 - exp(-2 beta J p_i p_j)) 2^32), p_i = s_i.r;
  *   cluster      canonical label = minimum site index in the cluster; the
- *                cluster flips iff bit 31 of flip word (label) is 1;
+ *                cluster flips iff bit (label) of the flip stream is 1;
  *                n-vector flip s <- s - 2 (s.r) r, then s <- s/|s|;
  *   measurement  after every sweep: E, m = |M|/N, m2 = m m, m4 = m2 m2,
  *                accumulated in FP64 with Neumaier compensation.
@@ -141,7 +146,9 @@ int pyro_get_state(pyro_handle h, void *host, size_t bytes);
 int pyro_set_state(pyro_handle h, const void *host, size_t bytes);
 
 /* Canonical cluster labels of the last sweep (the minimum site index of
- * each site's cluster), N int32 values.  Synchronises. */
+ * each site's cluster), N int32 values, computed on demand from the sweep's
+ * tile-local labels (the first call allocates a 4 N byte buffer).
+ * PYRO_E_STATE if the spins were set since the last sweep.  Synchronises. */
 int pyro_get_labels(pyro_handle h, int32_t *host, size_t bytes);
 
 /* Sweep counter: the sweep field of the Philox counter of the next sweep. */
@@ -168,11 +175,11 @@ uint64_t pyro_launch_count(pyro_handle h);
 
 /* Tracing: run n sweeps at beta like pyro_sweep, but as separate launches
  * bracketed by CUDA events, and return the mean device time in ms of each
- * of the five phases of a sweep in phase_ms[0..4]: tile-local labelling
- * (with bond activation), tile-crossing unions, flip, measurement,
- * accumulation.  Synchronises.  The chain advances exactly as with
- * pyro_sweep. */
-#define PYRO_NPHASE 5
+ * of the six phases of a sweep in phase_ms[0..5]: tile-local labelling
+ * (with bond activation), crossing-root init, crossing unions, flip,
+ * measurement, accumulation.  Synchronises.  The chain advances exactly as
+ * with pyro_sweep. */
+#define PYRO_NPHASE 6
 int pyro_profile_phases(pyro_handle h, double beta, int n, double *phase_ms);
 
 void pyro_destroy(pyro_handle h);
@@ -193,7 +200,8 @@ const char *pyro_last_error(void);
  * lattice with this seed and sweep counter (same conventions as above),
  * with every input and output supplied by the caller and all scratch memory
  * (flip bits, tile-crossing bond masks, per-block partial sums, the lattice
- * record and its statistics) taken from one file-scope device array of
+ * record and its statistics, the tile-local labels) taken from one
+ * file-scope device array of
  * PYRO_NOALLOC_SCRATCH_BYTES bytes.  That array exists on every GPU that
  * loads the library and stays there until the process exits.
  *
@@ -217,7 +225,7 @@ const char *pyro_last_error(void);
  * before returning, and returns PYRO_E_NOCONVERGE if a union-find loop hit
  * its bound. */
 #define PYRO_NOALLOC_MAX_L 64
-#define PYRO_NOALLOC_SCRATCH_BYTES 1606144
+#define PYRO_NOALLOC_SCRATCH_BYTES 9994752
 int pyro_ising_sweep_noalloc(const uint16_t *spins_in, uint16_t *spins_out, int32_t *labels, double *meas,
                              int L, double beta, uint64_t seed, uint64_t sweep, void *stream);
 

@@ -241,7 +241,7 @@ def pyro_launch_count(h) -> int:
     return int(lib().pyro_launch_count(h))
 
 
-PHASES = ("local", "boundary", "flip", "measure", "accumulate")
+PHASES = ("local", "binit", "bunite", "flip", "measure", "accumulate")
 
 
 def pyro_profile_phases(h, beta: float, n: int) -> dict:

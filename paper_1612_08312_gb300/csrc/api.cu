@@ -263,7 +263,8 @@ int pyro_get_labels(pyro_handle h, int32_t *host, size_t bytes)
     if (!h || !host) return fail(PYRO_E_INVAL, "NULL argument");
     if (bytes != (size_t)h->e.reps[0].N * sizeof(int32_t)) return fail(PYRO_E_INVAL, "labels need 4 N bytes");
     if (!h->e.labels_valid) return fail(PYRO_E_STATE, "no sweep since the spins were last set");
-    PYRO_CUDA(cudaMemcpyAsync(host, h->e.reps[0].P, bytes, cudaMemcpyDeviceToHost, h->e.stream), "labels copy");
+    PYRO_CUDA(h->e.compute_labels(), "labels");
+    PYRO_CUDA(cudaMemcpyAsync(host, h->e.reps[0].labels, bytes, cudaMemcpyDeviceToHost, h->e.stream), "labels copy");
     return finish(h->e);
 }
 

@@ -5,25 +5,30 @@
 // root under the smaller one (atomicMin on the larger root's parent), so the
 // root of a finished cluster is its minimum index -- the canonical label.
 // Two levels:
-//   * tile-local, in shared memory, over tile-local site indices (the local
-//     index order agrees with the global one inside a tile);
-//   * global, in HBM, over global site indices, for the bonds that cross a
-//     tile face.
-// Every loop is bounded by UF_MAX_ITERS; exceeding it sets a status bit
-// instead of spinning forever.
+//   * tile-local, in shared memory, over tile-local site indices (inside a
+//     tile the local index order agrees with the global one);
+//   * global, in HBM, over global site indices of the tile-local roots of
+//     clusters that cross a tile face.
+// Every loop is bounded; exceeding a bound sets a status bit instead of
+// spinning forever.
 #pragma once
 
 #include "pyro_internal.cuh"
 
 namespace pyro {
 
-__device__ __forceinline__ int sfind(volatile int *lab, int x)
+// Shared-memory slot of tile-local site v = 16 t + s: site-major across the
+// tile's cells, so that the 32 threads of a warp (consecutive cells t)
+// touch 32 consecutive words for any fixed s (no bank conflicts).
+__device__ __forceinline__ int lslot(int v, int nt) { return (v & 15) * nt + (v >> 4); }
+
+__device__ __forceinline__ int sfind(volatile int *lab, int x, int nt)
 {
-    int p = lab[x];
+    int p = lab[lslot(x, nt)];
 #pragma unroll 1
-    for (int it = 0; p != x && it < UF_MAX_ITERS; ++it) {
-        const int gp = lab[p];
-        if (gp != p) lab[x] = gp;  // path halving; gp is an ancestor of x
+    for (int it = 0; p != x && it < 65536; ++it) {
+        const int gp = lab[lslot(p, nt)];
+        if (gp != p) lab[lslot(x, nt)] = gp;  // path halving; gp is an ancestor of x
         x = p;
         p = gp;
     }
@@ -32,20 +37,20 @@ __device__ __forceinline__ int sfind(volatile int *lab, int x)
 
 // Union of the clusters of a and b in shared memory.  Returns false if the
 // iteration bound was hit.
-__device__ __forceinline__ bool sunite(int *lab, int a, int b)
+__device__ __forceinline__ bool sunite(int *lab, int a, int b, int nt)
 {
     volatile int *vl = lab;
 #pragma unroll 1
     for (int it = 0; it < 4096; ++it) {
-        a = sfind(vl, a);
-        b = sfind(vl, b);
+        a = sfind(vl, a, nt);
+        b = sfind(vl, b, nt);
         if (a == b) return true;
         if (a > b) {
             const int t = a;
             a = b;
             b = t;
         }
-        const int old = atomicMin(&lab[b], a);
+        const int old = atomicMin(&lab[lslot(b, nt)], a);
         if (old == b) return true;
         b = old;  // b had been linked meanwhile: unite a with its new parent
     }
@@ -57,7 +62,7 @@ __device__ __forceinline__ int gfind(const int *P, int x)
 {
     int p = __ldcg(P + x);
 #pragma unroll 1
-    for (int it = 0; p != x && it < UF_MAX_ITERS; ++it) {
+    for (int it = 0; p != x && it < (1 << 20); ++it) {
         x = p;
         p = __ldcg(P + x);
     }
@@ -83,38 +88,40 @@ __device__ __forceinline__ bool gunite(int *P, int a, int b)
     return false;
 }
 
-// Root of x once no union is in flight (plain cached loads).
+// Root of x once no union is in flight.
 __device__ __forceinline__ int root_of(const int *P, int x)
 {
     int p = P[x];
 #pragma unroll 1
-    for (int it = 0; p != x && it < UF_MAX_ITERS; ++it) {
+    for (int it = 0; p != x && it < (1 << 20); ++it) {
         x = p;
         p = P[x];
     }
     return x;
 }
 
-// Warp + block sum of a 64-bit counter into one of NSLOT global slots
-// (slots spread the atomics over many addresses).
-constexpr int NSLOT = 256;
-
-__device__ __forceinline__ void block_add_u64(unsigned long long v, unsigned long long *slots)
+// Components of a tetrahedron's four vertices under its six bond bits
+// (k = 0..5 pairs (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)): rr[v] = smallest
+// vertex connected to v.
+__device__ __forceinline__ void tet_components(uint32_t bits, int rr[4])
 {
-    __shared__ unsigned long long red_u64[32];
+    rr[0] = 0;
+    rr[1] = 1;
+    rr[2] = 2;
+    rr[3] = 3;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) red_u64[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        v = lane < nw ? red_u64[lane] : 0ull;
+    for (int pass = 0; pass < 3; ++pass)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && v) atomicAdd(slots + (blockIdx.x & (NSLOT - 1)), v);
-    }
+        for (int k = 0; k < 6; ++k)
+            if ((bits >> k) & 1u) {
+                const int m = min(rr[pair_a(k)], rr[pair_b(k)]);
+                rr[pair_a(k)] = m;
+                rr[pair_b(k)] = m;
+            }
 }
+
+// Pair index k of vertices (a, b), a < b.
+__device__ __forceinline__ int pair_index(int a, int b) { return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5); }
 
 // Deterministic block sum of a double (fixed shuffle tree), result valid in
 // thread 0.  Every thread of the block must call it.

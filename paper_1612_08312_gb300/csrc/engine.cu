@@ -11,6 +11,7 @@ namespace pyro {
 
 // ising.cu
 size_t ising_local_smem(const TileShape &t);
+void launch_labels(const Batch &B, int64_t ntiles, cudaStream_t s);
 cudaError_t ising_prepare(const TileShape &t);
 void ising_launch_init(const Batch &B, int64_t nblocks, int random, cudaStream_t s);
 void ising_launch_phase(int p, const Batch &B, int64_t ntiles, int64_t nblocks, cudaStream_t s);
@@ -167,7 +168,7 @@ std::string check_tile(const int *Ls, int R, int model, int prec, const TileShap
     for (int r = 0; r < R; ++r)
         if (Ls[r] % t.TX || Ls[r] % t.TY || Ls[r] % t.TZ) return "tile edges must divide every L";
     const int nt = t.TX * t.TY * t.TZ;
-    if (nt > (model == PYRO_ISING ? 1024 : 512)) return "tile has too many cells";
+    if (nt > 512) return "tile has too many cells (at most 512)";
     if (local_smem(model, prec, t) > 200 * 1024) return "tile needs too much shared memory";
     return "";
 }
@@ -230,6 +231,7 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
             size_t bytes;
         } al[] = {{&p.spins, spin_bytes_of(model, prec, p.N)},
                   {(void **)&p.P, (size_t)p.N * sizeof(int32_t)},
+                  {(void **)&p.L16, (size_t)p.N * sizeof(uint16_t)},
                   {(void **)&p.F, (size_t)p.ncells * sizeof(uint16_t)},
                   {(void **)&p.dmask, (size_t)p.ncells * sizeof(uint32_t)},
                   {(void **)&p.st, sizeof(DevStats)}};
@@ -300,14 +302,15 @@ cudaError_t Engine::set_beta(int r, double b)
     return cudaGetLastError();
 }
 
-// Phase p of a sweep: 0 local labelling, 1 boundary unions, 2 flip,
-// 3 measurement, 4 accumulation (mode as in accumulate_kernel).
+// Phase p of a sweep: 0 tile-local labelling (with bond activation),
+// 1 crossing-root init, 2 crossing unions, 3 flip, 4 measurement,
+// 5 accumulation (mode as in accumulate_kernel).
 void Engine::enqueue_phase(int p, int mode)
 {
-    if (p < 3) {
+    if (p < 4) {
         if (model == PYRO_ISING) ising_launch_phase(p, B, ntiles, nblocks, stream);
         else vec_launch_phase(p, model, prec, B, ntiles, nblocks, stream);
-    } else if (p == 3) {
+    } else if (p == 4) {
         if (model == PYRO_ISING) ising_launch_measure(B, nblocks, stream);
         else vec_launch_measure(model, prec, B, nblocks, stream);
     } else {
@@ -324,8 +327,27 @@ void Engine::enqueue_sweeps(int n)
 
 void Engine::enqueue_measure(int mode)
 {
-    enqueue_phase(3, mode);
     enqueue_phase(4, mode);
+    enqueue_phase(5, mode);
+}
+
+cudaError_t Engine::compute_labels()
+{
+    bool changed = false;
+    for (auto &r : reps)
+        if (!r.labels) {
+            const cudaError_t e = cudaMalloc(&r.labels, (size_t)r.N * sizeof(int32_t));
+            if (e != cudaSuccess) return e;
+            owned.push_back(r.labels);
+            changed = true;
+        }
+    if (changed) {
+        const cudaError_t e = cudaMemcpyAsync(d_reps, reps.data(), (size_t)R * sizeof(Rep), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return e;
+    }
+    launch_labels(B, ntiles, stream);
+    launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t Engine::profile(int n, double *phase_ms)
@@ -333,7 +355,7 @@ cudaError_t Engine::profile(int n, double *phase_ms)
     cudaEvent_t ev[NPHASE + 1];
     for (auto &x : ev)
         if (cudaEventCreate(&x) != cudaSuccess) return cudaGetLastError();
-    double acc[NPHASE] = {0, 0, 0, 0, 0};
+    double acc[NPHASE] = {};
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < n && e == cudaSuccess; ++s) {
         cudaEventRecord(ev[0], stream);

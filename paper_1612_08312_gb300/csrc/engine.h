@@ -10,9 +10,9 @@ namespace pyro {
 
 // Sweeps captured per CUDA graph for long runs.
 constexpr int GRAPH_CHUNK = 32;
-// Kernel launches (phases) per sweep: local labelling, boundary unions,
-// flip, measurement, accumulation.
-constexpr int NPHASE = 5;
+// Kernel launches (phases) per sweep: tile-local labelling, crossing-root
+// init, crossing unions, flip, measurement, accumulation.
+constexpr int NPHASE = 6;
 
 struct GraphEntry {
     int n;
@@ -45,6 +45,7 @@ struct Engine {
     cudaError_t measure();
     cudaError_t set_sweep(uint64_t s);
     cudaError_t set_trace(int r, int64_t cap);
+    cudaError_t compute_labels();
     int read_status(std::string &err);
     int launches_per_sweep() const;
 

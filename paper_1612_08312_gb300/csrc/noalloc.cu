@@ -7,8 +7,9 @@
 // synchronise the device and stall every other stream.  They pass their
 // inputs and outputs in, and the sweep's scratch memory (flip bits, tile-
 // crossing bond masks, per-block partial sums, the replica record and its
-// statistics) lives in the file-scope device array below instead of in
-// library allocations.
+// statistics, the tile-local labels) lives in the file-scope device array
+// below instead of in library allocations.  The caller's label buffer is
+// the union-find workspace and receives the canonical labels at the end.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -19,6 +20,7 @@
 namespace pyro {
 
 void ising_launch_phase(int p, const Batch &B, int64_t ntiles, int64_t nblocks, cudaStream_t s);
+void launch_labels(const Batch &B, int64_t ntiles, cudaStream_t s);
 void ising_launch_measure(const Batch &B, int64_t nblocks, cudaStream_t s);
 void launch_accumulate(const Batch &B, bool ising, int mode, int nc, cudaStream_t s);
 void set_error(const std::string &msg);
@@ -33,7 +35,8 @@ constexpr size_t NA_OFF_STATS = 256;
 constexpr size_t NA_OFF_F = 512;
 constexpr size_t NA_OFF_DMASK = NA_OFF_F + (size_t)NA_MAX_CELLS * sizeof(uint16_t);
 constexpr size_t NA_OFF_PARTIALS = NA_OFF_DMASK + (size_t)NA_MAX_CELLS * sizeof(uint32_t);
-constexpr size_t NA_BYTES = NA_OFF_PARTIALS + (size_t)NA_MAX_BLOCKS * 4 * sizeof(double);
+constexpr size_t NA_OFF_L16 = NA_OFF_PARTIALS + (size_t)NA_MAX_BLOCKS * 4 * sizeof(double);
+constexpr size_t NA_BYTES = NA_OFF_L16 + (size_t)16 * NA_MAX_CELLS * sizeof(uint16_t);
 static_assert(sizeof(Rep) <= 256 && sizeof(DevStats) <= 256, "scratch header slots too small");
 static_assert(NA_BYTES == PYRO_NOALLOC_SCRATCH_BYTES, "scratch size differs from the header");
 
@@ -97,6 +100,8 @@ extern "C" int pyro_ising_sweep_noalloc(const uint16_t *spins_in, uint16_t *spin
     Rep rep = {};
     rep.spins = spins_out;
     rep.P = labels;
+    rep.labels = labels;
+    rep.L16 = reinterpret_cast<uint16_t *>(base + NA_OFF_L16);
     rep.F = reinterpret_cast<uint16_t *>(base + NA_OFF_F);
     rep.dmask = reinterpret_cast<uint32_t *>(base + NA_OFF_DMASK);
     rep.st = reinterpret_cast<DevStats *>(base + NA_OFF_STATS);
@@ -128,9 +133,13 @@ extern "C" int pyro_ising_sweep_noalloc(const uint16_t *spins_in, uint16_t *spin
         if (e != cudaSuccess) return na_fail(PYRO_E_CUDA, std::string("spin copy: ") + cudaGetErrorString(e));
     }
     na_setup_kernel<<<1, 1, 0, s>>>(rep, reinterpret_cast<Rep *>(base + NA_OFF_REP), rep.st, sweep);
-    for (int p = 0; p < 3; ++p) ising_launch_phase(p, B, ntiles, nblocks, s);
+    for (int p = 0; p < 4; ++p) ising_launch_phase(p, B, ntiles, nblocks, s);
     ising_launch_measure(B, nblocks, s);
     launch_accumulate(B, true, 2, 1, s);
+    // canonical labels written over the union-find workspace: every value
+    // written is the root of that site, so a chain still being followed by
+    // another thread stays valid
+    launch_labels(B, ntiles, s);
     e = cudaMemcpyAsync(meas, rep.st->last, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(PYRO_E_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));

@@ -19,6 +19,7 @@ constexpr uint32_t TAG_BOND = 1u;
 constexpr uint32_t TAG_FLIP = 2u;
 constexpr uint32_t TAG_AXIS = 3u;
 constexpr uint32_t TAG_INIT = 4u;
+constexpr uint32_t TAG_TIE = 5u;
 constexpr uint32_t INIT_SWEEP_FIELD = 0xFFFFFFFFu;
 constexpr int MAX_AXIS_ATTEMPTS = 256;
 
@@ -111,9 +112,12 @@ struct TileShape {
 // One lattice (replica) as the kernels see it.
 struct Rep {
     void *spins;       // Ising: uint16 per cell; n-vector: n planes of N values
-    int32_t *P;        // union-find parents; canonical labels after a sweep
-    uint16_t *F;       // flip bits of tile-local roots, one word per cell
-    uint32_t *dmask;   // active tile-crossing bonds of face cells (24 bits)
+    uint16_t *L16;     // per site: tile-local index of its tile-local root;
+                       // bit 15 set on a root whose cluster crosses a tile face
+    int32_t *P;        // global union-find parents, used at crossing roots only
+    uint16_t *F;       // the sweep's flip bit of every site, one word per cell
+    uint32_t *dmask;   // union pairs of face cells that cross the tile (24 bits)
+    int32_t *labels;   // canonical labels (filled on demand), or NULL
     DevStats *st;
     double *trace;     // ring buffer of (E, m2, m4, M_x), or NULL
     int64_t trace_cap;

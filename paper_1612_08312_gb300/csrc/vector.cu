@@ -6,7 +6,8 @@
 // reflect their spins, s -> s - 2 (s.r) r.
 //
 // Spins are stored as n component planes of N values of T (float or
-// double).  The FP64 path uses explicitly rounded IEEE operations in the
+// double).  A bond with p_i p_j > 0 is active iff its 32-bit uniform
+// w < floor(p 2^32), w drawn like the Ising bonds' (sweep_core.cuh).  The FP64 path uses explicitly rounded IEEE operations in the
 // same order as the definition, so projections, reflections and the axis
 // are bit-identical to a straightforward FP64 evaluation without fused
 // multiply-add.  The FP32 path stores and updates spins in float; its
@@ -14,10 +15,10 @@
 //
 // Kernels (each over a Batch of lattices): vec_local (projections of the
 // tile + halo staged in shared memory, bond activation, tile-local
-// labelling), the global union of tile-crossing bonds (boundary_kernel,
+// labelling), the global union of tile-crossing clusters (boundary_kernel,
 // shared with the Ising sweep), vec_flip (root, flip, reflection) and
 // vec_measure (E and M per block in FP64).
-#include "ccl.cuh"
+#include "sweep_core.cuh"
 
 namespace pyro {
 
@@ -32,10 +33,6 @@ struct Ar<double> {
     static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
     static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
     static __device__ __forceinline__ double bond_p(double K2, double x) { return -expm1(-__dmul_rn(K2, x)); }
-    static __device__ __forceinline__ double uword(uint32_t w)
-    {
-        return __dmul_rn(__dadd_rn((double)w, 0.5), 2.3283064365386962890625e-10);
-    }
 };
 
 template <>
@@ -46,10 +43,6 @@ struct Ar<float> {
     static __device__ __forceinline__ float div(float a, float b) { return a / b; }
     static __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
     static __device__ __forceinline__ float bond_p(float K2, float x) { return -expm1f(-(K2 * x)); }
-    static __device__ __forceinline__ float uword(uint32_t w)
-    {
-        return ((float)w + 0.5f) * 2.3283064365386962890625e-10f;
-    }
 };
 
 // Uniform unit vector from the (seed, sweep, tag) stream, FP64 with
@@ -95,21 +88,44 @@ __device__ __forceinline__ T project(const T *spins, int64_t N, int64_t i, const
     return p;
 }
 
+// Threshold of a bond with activation probability p: active iff its 32-bit
+// uniform w < floor(p 2^32) (p = 1 gives 2^32).
+__device__ __forceinline__ uint64_t prob_threshold(double p)
+{
+    if (!(p > 0.0)) return 0;
+    const double t = floor(__dmul_rn(p, 4294967296.0));
+    return t >= 4294967296.0 ? (1ull << 32) : (uint64_t)t;
+}
+
+__device__ __forceinline__ uint64_t prob_threshold(float p)
+{
+    if (!(p > 0.0f)) return 0;
+    const float t = floorf(p * 4294967296.0f);
+    return t >= 4294967296.0f ? (1ull << 32) : (uint64_t)__float2ull_rz(t);
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t vec_halo_bytes(int TX, int TY, int TZ)
+{
+    return (size_t)16 * (TX + 1) * (TY + 1) * (TZ + 1) * sizeof(T);
+}
+
 template <int NC, typename T>
 __global__ void __launch_bounds__(512) vec_local_kernel(const __grid_constant__ Batch B)
 {
     using A = Ar<T>;
-    extern __shared__ int smem[];
+    extern __shared__ __align__(16) int smem[];
     const int rep = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[rep];
-    const T *spins = static_cast<const T *>(R.spins);
-    const int L = R.L;
+    const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[rep]);
+    const int nt = c.nt, L = c.L;
     const int64_t N = R.N;
-    const int TX = B.TX, TY = B.TY, TZ = B.TZ;
-    const int nt = TX * TY * TZ;
-    const int HX = TX + 1, HY = TY + 1, HZ = TZ + 1;
     int *lab = smem;
-    T *proj = reinterpret_cast<T *>(smem + 16 * nt + ((16 * nt) & 1));
+    uint32_t *plist = reinterpret_cast<uint32_t *>(smem + 16 * nt);
+    int *pcount = smem + 28 * nt;
+    T *proj = reinterpret_cast<T *>(smem + 28 * nt + 4);
+    const int HX = c.TX + 1, HY = c.TY + 1, HZ = c.TZ + 1;
+    const T *spins = static_cast<const T *>(R.spins);
     const uint32_t sweep = (uint32_t)R.st->sweep;
     const uint64_t seed = R.seed;
 
@@ -117,15 +133,11 @@ __global__ void __launch_bounds__(512) vec_local_kernel(const __grid_constant__ 
     unit_vector_dev<NC>(seed, sweep, TAG_AXIS, 0, rd);
     const T r[3] = {(T)rd[0], (T)rd[1], (T)rd[2]};
 
-    const int64_t tile = blockIdx.x - B.tile_begin[rep];
-    const int ox = (int)(tile % R.ntx) * TX;
-    const int oy = (int)((tile / R.ntx) % R.nty) * TY;
-    const int oz = (int)(tile / ((int64_t)R.ntx * R.nty)) * TZ;
-
+    // projections s_i . r of the tile's sites and the backward halo
     for (int idx = threadIdx.x; idx < 16 * HX * HY * HZ; idx += blockDim.x) {
         const int h = idx >> 4, s = idx & 15;
         const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-        int gx = ox + hx - 1, gy = oy + hy - 1, gz = oz + hz - 1;
+        int gx = c.ox + hx - 1, gy = c.oy + hy - 1, gz = c.oz + hz - 1;
         gx += (gx < 0) ? L : 0;
         gy += (gy < 0) ? L : 0;
         gz += (gz < 0) ? L : 0;
@@ -134,163 +146,72 @@ __global__ void __launch_bounds__(512) vec_local_kernel(const __grid_constant__ 
     }
     __syncthreads();
 
-    const int t = threadIdx.x;
-    const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
-    const int x = ox + lx, y = oy + ly, z = oz + lz;
-    const int64_t cell = (int64_t)x + (int64_t)L * ((int64_t)y + (int64_t)L * z);
+    // halo cell of the vertex at backward-shift mask m
+    auto hidx = [&](int m) {
+        return (c.lx + 1 - (m & 1)) + HX * ((c.ly + 1 - ((m >> 1) & 1)) + HY * (c.lz + 1 - ((m >> 2) & 1)));
+    };
     const T K2 = (T)R.K2;
-
-    uint32_t dn_act = 0;
+    uint64_t act = 0;
+    if (R.K2 > 0.0) {
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        T pu[4], pd[4];
+        for (int q = 0; q < 6; ++q) {
+            T xq[8];
+            uint32_t pos = 0;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            pu[v] = proj[16 * ((lx + 1) + HX * ((ly + 1) + HY * (lz + 1))) + 4 * f + v];
-            const int m = down_mask(f, v);
-            const int hidx = (lx + 1 - (m & 1)) + HX * ((ly + 1 - ((m >> 1) & 1)) + HY * (lz + 1 - ((m >> 2) & 1)));
-            pd[v] = proj[16 * hidx + down_bit(f, v)];
-        }
-        T xb[12];
-        uint32_t pos = 0;
+            for (int h = 0; h < 8; ++h) {
+                const int cb = 8 * q + h, f = cb / 12, k = cb % 12;
+                const bool up = k < 6;
+                const int kk = up ? k : k - 6;
+                const int va = pair_a(kk), vb = pair_b(kk);
+                const T pa = up ? proj[16 * hidx(0) + 4 * f + va] : proj[16 * hidx(down_mask(f, va)) + down_bit(f, va)];
+                const T pb = up ? proj[16 * hidx(0) + 4 * f + vb] : proj[16 * hidx(down_mask(f, vb)) + down_bit(f, vb)];
+                xq[h] = A::mul(pa, pb);
+                pos |= (xq[h] > (T)0 ? 1u : 0u) << h;
+            }
+            if (!pos) continue;
+            const uint64_t j = 6 * (uint64_t)c.cell + q;
+            const uint4 wd = philox_call(seed, sweep, TAG_BOND, j);
+            const uint32_t ww[4] = {wd.x, wd.y, wd.z, wd.w};
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            xb[k] = A::mul(pu[pair_a(k)], pu[pair_b(k)]);
-            xb[6 + k] = A::mul(pd[pair_a(k)], pd[pair_b(k)]);
-        }
-#pragma unroll
-        for (int k = 0; k < 12; ++k) pos |= (xb[k] > (T)0 ? 1u : 0u) << k;
-
-        uint32_t act = 0;
-        if (R.K2 > 0.0) {
-            const uint64_t rr_fcc = 4 * (uint64_t)cell + f;
-#pragma unroll
-            for (int g = 0; g < 3; ++g) {
-                if ((pos >> (4 * g)) & 0xFu) {
-                    const uint4 wd = philox_call(seed, sweep, TAG_BOND, 3 * rr_fcc + g);
-                    const uint32_t ww[4] = {wd.x, wd.y, wd.z, wd.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int k = 4 * g + q;
-                        if ((pos >> k) & 1u) {
-                            const T p = A::bond_p(K2, xb[k]);
-                            act |= (A::uword(ww[q]) < p ? 1u : 0u) << k;
-                        }
-                    }
+            for (int h = 0; h < 8; ++h) {
+                if (!((pos >> h) & 1u)) continue;
+                const HalfCompare hc(prob_threshold(A::bond_p(K2, xq[h])));
+                const uint32_t hi = (ww[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
+                bool a = hc.all || hi < hc.thi;
+                if (!hc.all && hi == hc.thi) {
+                    const uint4 wt = philox_call(seed, sweep, TAG_TIE, j);
+                    a = ((word_of(wt, h >> 1) >> (16 * (h & 1))) & 0xFFFFu) < hc.tlo;
                 }
+                act |= (uint64_t)(a ? 1u : 0u) << (8 * q + h);
             }
         }
-
-        int rr[4] = {0, 1, 2, 3};
-#pragma unroll
-        for (int pass = 0; pass < 3; ++pass)
-#pragma unroll
-            for (int k = 0; k < 6; ++k)
-                if ((act >> k) & 1u) {
-                    const int m = min(rr[pair_a(k)], rr[pair_b(k)]);
-                    rr[pair_a(k)] = m;
-                    rr[pair_b(k)] = m;
-                }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) lab[16 * t + 4 * f + v] = 16 * t + 4 * f + rr[v];
-        dn_act |= ((act >> 6) & 63u) << (6 * f);
     }
-    __syncthreads();
-
-    const int lxb = lx > 0 ? lx - 1 : (TX == L ? TX - 1 : -1);
-    const int lyb = ly > 0 ? ly - 1 : (TY == L ? TY - 1 : -1);
-    const int lzb = lz > 0 ? lz - 1 : (TZ == L ? TZ - 1 : -1);
-    uint32_t cross = 0;
-    bool ok = true;
-    uint32_t todo = dn_act;
-    while (todo) {
-        const int bit = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int f = bit / 6, k = bit % 6;
-        int loc[2];
-        bool inside = true;
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int v = e == 0 ? pair_a(k) : pair_b(k);
-            const int m = down_mask(f, v);
-            const int cx = (m & 1) ? lxb : lx, cy = (m & 2) ? lyb : ly, cz = (m & 4) ? lzb : lz;
-            if (cx < 0 || cy < 0 || cz < 0) inside = false;
-            loc[e] = 16 * (cx + TX * (cy + TY * cz)) + down_bit(f, v);
-        }
-        if (inside) ok &= sunite(lab, loc[0], loc[1]);
-        else cross |= 1u << bit;
-    }
-    if (lx == 0 || ly == 0 || lz == 0) R.dmask[cell] = cross;
-    if (!ok) atomicOr(&R.st->status, ST_NOCONVERGE);
-    __syncthreads();
-
-    int root_g[16];
-    uint32_t is_root = 0;
-#pragma unroll
-    for (int s = 0; s < 16; ++s) {
-        const int me = 16 * t + s;
-        const int rl = sfind(lab, me);
-        is_root |= (rl == me ? 1u : 0u) << s;
-        const int rc = rl >> 4;
-        const int rx = ox + rc % TX, ry = oy + (rc / TX) % TY, rz = oz + rc / (TX * TY);
-        root_g[s] = 16 * (rx + L * (ry + L * rz)) + (rl & 15);
-    }
-    int4 *P4 = reinterpret_cast<int4 *>(R.P + 16 * cell);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        P4[q] = make_int4(root_g[4 * q], root_g[4 * q + 1], root_g[4 * q + 2], root_g[4 * q + 3]);
-    uint32_t fb = 0;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        if ((is_root >> (4 * f)) & 0xFu) {
-            const uint4 wd = philox_call(seed, sweep, TAG_FLIP, 4 * (uint64_t)cell + f);
-            fb |= ((wd.x >> 31) | ((wd.y >> 31) << 1) | ((wd.z >> 31) << 2) | ((wd.w >> 31) << 3)) << (4 * f);
-        }
-    }
-    R.F[cell] = (uint16_t)(fb & is_root);
+    local_core(c, R, act, sweep, lab, plist, pcount);
 }
 
 template <int NC, typename T>
-__global__ void __launch_bounds__(CELL_BLOCK) vec_flip_kernel(const __grid_constant__ Batch B)
+__global__ void __launch_bounds__(512) vec_flip_kernel(const __grid_constant__ Batch B)
 {
     using A = Ar<T>;
-    const int rep = find_rep(B.block_begin, B.R, blockIdx.x);
+    extern __shared__ __align__(16) int smem[];
+    const int rep = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[rep];
-    const int64_t cell = (blockIdx.x - B.block_begin[rep]) * CELL_BLOCK + threadIdx.x;
-    if (cell >= R.ncells) return;
+    const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[rep]);
+    uint16_t *ls = reinterpret_cast<uint16_t *>(smem);
+    uint16_t *fs = ls + 16 * c.nt;
+    int root[16];
+    uint32_t flip;
+    resolve_cell(c, R, ls, fs, root, flip);
+    if (!flip) return;
     double rd[3];
     unit_vector_dev<NC>(R.seed, (uint32_t)R.st->sweep, TAG_AXIS, 0, rd);
     const T r[3] = {(T)rd[0], (T)rd[1], (T)rd[2]};
     T *spins = static_cast<T *>(R.spins);
-    const int32_t *P = R.P;
-    int4 *P4 = reinterpret_cast<int4 *>(R.P + 16 * cell);
-    int p[16];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int4 v = P4[q];
-        p[4 * q] = v.x;
-        p[4 * q + 1] = v.y;
-        p[4 * q + 2] = v.z;
-        p[4 * q + 3] = v.w;
-    }
-    bool changed = false;
-    uint32_t flip = 0;
-#pragma unroll
-    for (int s = 0; s < 16; ++s) {
-        const int rt = root_of(P, p[s]);
-        flip |= ((uint32_t)(R.F[rt >> 4] >> (rt & 15)) & 1u) << s;
-        changed |= (rt != p[s]);
-        p[s] = rt;
-    }
-    if (changed) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) P4[q] = make_int4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
-    }
     const int64_t N = R.N;
     while (flip) {
         const int s = __ffs(flip) - 1;
         flip &= flip - 1;
-        const int64_t i = 16 * cell + s;
+        const int64_t i = 16 * c.cell + s;
         const T pr = project<NC, T>(spins, N, i, r);
         const T d2 = A::mul((T)2, pr);
         T sv[3];
@@ -385,33 +306,38 @@ __global__ void __launch_bounds__(CELL_BLOCK) vec_init_kernel(const __grid_const
 }
 
 // ------------------------------------------------------------ launchers --
+size_t resolve_smem(const TileShape &t);
+void launch_boundary(int unite, const Batch &B, int64_t ntiles, cudaStream_t s);
+
 size_t vec_local_smem(const TileShape &t, int prec)
 {
     const int nt = t.TX * t.TY * t.TZ;
-    const size_t es = prec == PYRO_FP64 ? 8 : 4;
-    return (size_t)(16 * nt + ((16 * nt) & 1)) * sizeof(int) +
-           (size_t)16 * (t.TX + 1) * (t.TY + 1) * (t.TZ + 1) * es;
+    return core_smem_bytes(nt) +
+           (prec == PYRO_FP64 ? vec_halo_bytes<double>(t.TX, t.TY, t.TZ) : vec_halo_bytes<float>(t.TX, t.TY, t.TZ));
 }
-
-void launch_boundary(const Batch &B, int64_t ntiles, cudaStream_t s);
 
 template <int NC, typename T>
 struct VecOps {
     static cudaError_t prepare(const TileShape &t, int prec)
     {
-        return cudaFuncSetAttribute(vec_local_kernel<NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)vec_local_smem(t, prec));
+        cudaError_t e = cudaFuncSetAttribute(vec_local_kernel<NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)vec_local_smem(t, prec));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(vec_flip_kernel<NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)resolve_smem(t));
+        return e;
     }
     static void init(const Batch &B, int64_t nblocks, int random, cudaStream_t s)
     {
         vec_init_kernel<NC, T><<<(unsigned)nblocks, CELL_BLOCK, 0, s>>>(B, random);
     }
-    static void phase(int p, const Batch &B, int64_t ntiles, int64_t nblocks, int prec, cudaStream_t s)
+    static void phase(int p, const Batch &B, int64_t ntiles, int prec, cudaStream_t s)
     {
         const TileShape t{B.TX, B.TY, B.TZ};
-        if (p == 0) vec_local_kernel<NC, T><<<(unsigned)ntiles, B.TX * B.TY * B.TZ, vec_local_smem(t, prec), s>>>(B);
-        else if (p == 1) launch_boundary(B, ntiles, s);
-        else vec_flip_kernel<NC, T><<<(unsigned)nblocks, CELL_BLOCK, 0, s>>>(B);
+        const int nt = B.TX * B.TY * B.TZ;
+        if (p == 0) vec_local_kernel<NC, T><<<(unsigned)ntiles, nt, vec_local_smem(t, prec), s>>>(B);
+        else if (p == 1 || p == 2) launch_boundary(p == 2, B, ntiles, s);
+        else vec_flip_kernel<NC, T><<<(unsigned)ntiles, nt, resolve_smem(t), s>>>(B);
     }
     static void measure(const Batch &B, int64_t nblocks, cudaStream_t s)
     {
@@ -439,10 +365,12 @@ void vec_launch_init(int model, int prec, const Batch &B, int64_t nblocks, int r
     PYRO_VEC_DISPATCH(model, prec, init(B, nblocks, random, s));
 }
 
-// Phase p of a sweep: 0 local labelling, 1 boundary unions, 2 flip.
+// Phase p of a sweep: 0 local labelling, 1 boundary init, 2 boundary unite,
+// 3 flip.
 void vec_launch_phase(int p, int model, int prec, const Batch &B, int64_t ntiles, int64_t nblocks, cudaStream_t s)
 {
-    PYRO_VEC_DISPATCH(model, prec, phase(p, B, ntiles, nblocks, prec, s));
+    PYRO_VEC_DISPATCH(model, prec, phase(p, B, ntiles, prec, s));
+    (void)nblocks;
 }
 
 void vec_launch_measure(int model, int prec, const Batch &B, int64_t nblocks, cudaStream_t s)

@@ -40,7 +40,7 @@ def test_small_lattices_every_sweep(L, start):
 
 
 @pytest.mark.parametrize("tile", [(1, 1, 1), (2, 2, 2), (4, 2, 1), (2, 4, 8), (8, 8, 4), (8, 8, 8), (16, 8, 4),
-                                  (16, 16, 4)])
+                                  (16, 16, 2)])
 def test_tile_shapes(tile):
     run_pair(16, 4.21394, seed=3, start="random", sweeps=4, tile=tile)
 
@@ -52,6 +52,12 @@ def test_temperatures_l12(T):
 
 def test_l24_many_tiles():
     run_pair(24, 4.21394, seed=5, start="random", sweeps=3)
+
+
+def test_tile_over_512_cells_is_rejected():
+    with pytest.raises(pyro.PyroError) as ei:
+        pyro.Lattice(16, pyro.ISING, 1, tile=(16, 16, 4))
+    assert ei.value.code == pyro.E_INVAL
 
 
 def test_beta_zero_has_no_active_bond():
