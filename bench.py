@@ -40,14 +40,13 @@ SWEEP_BYTES_PER_SITE = 8.25
 # Bytes per site each phase of the Ising sweep must move in HBM.
 PHASE_BYTES_PER_SITE = {
     "local": 0.125 + 2.0 + 0.125,   # spin words read; 16-bit local labels and flip words written
-    "binit": 0.0,                   # only tile-crossing pairs; not credited
-    "bunite": 0.0,
+    "boundary": 0.0,                # only tile-crossing pairs; not credited
     "flip": 2.0 + 0.125 + 0.25,     # local labels and flip words read; spin words read and written
     "measure": 0.125,               # spin words read
     "accumulate": 0.0,
 }
-KERNEL_NAMES = {"local": "ising_local_kernel", "binit": "boundary_kernel<false>", "bunite": "boundary_kernel<true>",
-                "flip": "ising_flip_kernel", "measure": "ising_measure_kernel", "accumulate": "accumulate_kernel"}
+KERNEL_NAMES = {"local": "ising_local_kernel", "boundary": "boundary_kernel", "flip": "ising_flip_kernel",
+                "measure": "ising_measure_kernel", "accumulate": "accumulate_kernel"}
 
 
 def peaks():

@@ -19,19 +19,22 @@
  *   site index   i = 16 (x + L (y + L z)) + 4 f + mu, position (quarter
  *                cell units) 4 (x,y,z) + A_f + B_mu, A = {0,(0,2,2),(2,0,2),
  *                (2,2,0)}, B = {0,(0,1,1),(1,0,1),(1,1,0)};
- *   bond id      b = 12 r + k, r = i >> 2; k = 0..5 the pairs (0,1) (0,2)
- *                (0,3) (1,2) (1,3) (2,3) of basis vertices of the tetrahedron
- *                of FCC point r, k = 6..11 the same pairs of the other
- *                tetrahedron through site 4r;
+ *   bond id      the bonds of cell c are numbered b = 48 c + 16 g + 4 f + q,
+ *                f the FCC point of the tetrahedron, (g, q) = (0,0) up
+ *                pair (0,1), (0,1) up (1,2), (0,2) up (2,3), (0,3) up (0,3),
+ *                (1,0) up (0,2), (1,1) up (1,3), (1,2) down (0,2), (1,3) down
+ *                (1,3), (2,0) down (0,1), (2,1) down (1,2), (2,2) down (2,3),
+ *                (2,3) down (0,3) (pairs of basis vertices);
  *   random bits  Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
  *                (j_lo, j_hi, sweep, tag); tags 1 bond, 2 flip, 3 axis,
  *                4 initial state (sweep field 0xFFFFFFFF), 5 tie.  A call's
- *                128 bits are read as eight 16-bit halves (half h: bits
- *                16 (h & 1).. of output word h >> 1) or as 128 bits (bit t:
- *                bit t & 31 of output word t >> 5);
- *   bond uniform w_b = (half b & 7 of bond call b >> 3) << 16 | (half b & 7
- *                of tie call b >> 3); the tie half is only needed when the
- *                high halves of w_b and the threshold are equal;
+ *                128 bits are read as 16 bytes (byte t: bits 8 (t & 3).. of
+ *                output word t >> 2), 4 words, or 128 bits (bit t: bit t & 31
+ *                of output word t >> 5);
+ *   bond uniform w_b = (byte b & 15 of bond call b >> 4) << 24 | (low 24
+ *                bits of word b & 3 of tie call b >> 2); the tie bits are
+ *                only needed when the top bytes of w_b and the threshold are
+ *                equal;
  *   Ising bond   active iff s_i = s_j and w_b < floor((1 - exp(-2 beta J))
  *                2^32);
  *   n-vector     axis r drawn once per sweep; active iff p_i p_j > 0 and
@@ -175,11 +178,11 @@ uint64_t pyro_launch_count(pyro_handle h);
 
 /* Tracing: run n sweeps at beta like pyro_sweep, but as separate launches
  * bracketed by CUDA events, and return the mean device time in ms of each
- * of the six phases of a sweep in phase_ms[0..5]: tile-local labelling
- * (with bond activation), crossing-root init, crossing unions, flip,
+ * of the five phases of a sweep in phase_ms[0..4]: tile-local labelling
+ * (with bond activation), unions of clusters crossing tile faces, flip,
  * measurement, accumulation.  Synchronises.  The chain advances exactly as
  * with pyro_sweep. */
-#define PYRO_NPHASE 6
+#define PYRO_NPHASE 5
 int pyro_profile_phases(pyro_handle h, double beta, int n, double *phase_ms);
 
 void pyro_destroy(pyro_handle h);
@@ -200,8 +203,8 @@ const char *pyro_last_error(void);
  * lattice with this seed and sweep counter (same conventions as above),
  * with every input and output supplied by the caller and all scratch memory
  * (flip bits, tile-crossing bond masks, per-block partial sums, the lattice
- * record and its statistics, the tile-local labels) taken from one
- * file-scope device array of
+ * record and its statistics, the tile-local labels, the links between
+ * clusters that cross tile faces) taken from one file-scope device array of
  * PYRO_NOALLOC_SCRATCH_BYTES bytes.  That array exists on every GPU that
  * loads the library and stays there until the process exits.
  *
@@ -209,7 +212,6 @@ const char *pyro_last_error(void);
  *   spins_out  device, L^3 uint16: the spins after the sweep (may equal
  *              spins_in for an in-place update)
  *   labels     device, 16 L^3 int32: canonical cluster labels of the sweep
- *              (also used as the union-find workspace)
  *   meas       device, 4 doubles: E, m^2, m^4 and M of the new configuration
  *   L          1 <= L <= PYRO_NOALLOC_MAX_L, else PYRO_E_INVAL
  *   beta, seed, sweep   inverse temperature (J = 1), Philox key, sweep field
@@ -224,8 +226,8 @@ const char *pyro_last_error(void);
  * array and must be serialised by the caller.  Synchronises the stream
  * before returning, and returns PYRO_E_NOCONVERGE if a union-find loop hit
  * its bound. */
-#define PYRO_NOALLOC_MAX_L 64
-#define PYRO_NOALLOC_SCRATCH_BYTES 9994752
+#define PYRO_NOALLOC_MAX_L 32
+#define PYRO_NOALLOC_SCRATCH_BYTES 6488576
 int pyro_ising_sweep_noalloc(const uint16_t *spins_in, uint16_t *spins_out, int32_t *labels, double *meas,
                              int L, double beta, uint64_t seed, uint64_t sweep, void *stream);
 

@@ -241,7 +241,7 @@ def pyro_launch_count(h) -> int:
     return int(lib().pyro_launch_count(h))
 
 
-PHASES = ("local", "binit", "bunite", "flip", "measure", "accumulate")
+PHASES = ("local", "boundary", "flip", "measure", "accumulate")
 
 
 def pyro_profile_phases(h, beta: float, n: int) -> dict:
@@ -310,7 +310,7 @@ def pyro_batch_destroy(b):
     lib().pyro_batch_destroy(b)
 
 
-NOALLOC_MAX_L = 64
+NOALLOC_MAX_L = 32
 
 
 def pyro_ising_sweep_noalloc(spins_in: int, spins_out: int, labels: int, meas: int, L: int, beta: float,

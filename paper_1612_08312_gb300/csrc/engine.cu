@@ -14,16 +14,16 @@ size_t ising_local_smem(const TileShape &t);
 void launch_labels(const Batch &B, int64_t ntiles, cudaStream_t s);
 cudaError_t ising_prepare(const TileShape &t);
 void ising_launch_init(const Batch &B, int64_t nblocks, int random, cudaStream_t s);
-void ising_launch_phase(int p, const Batch &B, int64_t ntiles, int64_t nblocks, cudaStream_t s);
-void ising_launch_measure(const Batch &B, int64_t nblocks, cudaStream_t s);
+void ising_launch_phase(int p, const Batch &B, int64_t ntiles, cudaStream_t s);
+void ising_launch_measure(const Batch &B, int64_t ntiles, cudaStream_t s);
 // vector.cu
 size_t vec_local_smem(const TileShape &t, int prec);
 cudaError_t vec_prepare(int model, int prec, const TileShape &t);
 void vec_launch_init(int model, int prec, const Batch &B, int64_t nblocks, int random, cudaStream_t s);
-void vec_launch_phase(int p, int model, int prec, const Batch &B, int64_t ntiles, int64_t nblocks, cudaStream_t s);
-void vec_launch_measure(int model, int prec, const Batch &B, int64_t nblocks, cudaStream_t s);
+void vec_launch_phase(int p, int model, int prec, const Batch &B, int64_t ntiles, cudaStream_t s);
+void vec_launch_measure(int model, int prec, const Batch &B, int64_t ntiles, cudaStream_t s);
 
-// Per replica (one block each): reduce the per-block partials of the
+// Per replica (one block each): reduce the per-tile partials of the
 // measurement kernel in a fixed order, form E, m = |M|/N, m^2, m^4 (Eq. 1,
 // Eq. 2) and, in mode 1, add them to the Neumaier sums, append the trace
 // record and advance the sweep counter; mode 2 only records them as the last
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(1024) accumulate_kernel(const __grid_constant_
     const int r = blockIdx.x;
     const Rep &R = B.reps[r];
     DevStats *st = R.st;
-    const int64_t b0 = B.block_begin[r], b1 = B.block_begin[r + 1];
+    const int64_t b0 = B.tile_begin[r], b1 = B.tile_begin[r + 1];
     double tot[4] = {0.0, 0.0, 0.0, 0.0};
     if (ISING) {
         __shared__ unsigned long long su[2][1024];
@@ -98,6 +98,8 @@ __global__ void __launch_bounds__(1024) accumulate_kernel(const __grid_constant_
     }
     st->count += 1;
     st->sweep += 1;
+    st->last_epoch = st->epoch;
+    st->epoch += 1;
 }
 
 __global__ void set_params_kernel(Rep *reps, int r, uint64_t thr, double K2)
@@ -117,6 +119,14 @@ __global__ void set_sweep_kernel(const __grid_constant__ Batch B, unsigned long 
     if ((int)threadIdx.x < B.R) B.reps[threadIdx.x].st->sweep = sweep;
 }
 
+__global__ void reset_epoch_kernel(const __grid_constant__ Batch B)
+{
+    if ((int)threadIdx.x < B.R) {
+        B.reps[threadIdx.x].st->epoch = 0;
+        B.reps[threadIdx.x].st->last_epoch = 0xFFFFFFFFull;
+    }
+}
+
 // Host launcher of the accumulation kernel for callers outside this file.
 void launch_accumulate(const Batch &B, bool ising, int mode, int nc, cudaStream_t s)
 {
@@ -134,12 +144,22 @@ uint64_t ising_threshold(double beta, double J)
     return tq >= 4294967296.0 ? (1ull << 32) : (uint64_t)tq;
 }
 
-static int divisor_at_most(int L, int cap)
+// Largest power of two that divides L and is at most cap.
+static int pow2_divisor_at_most(int L, int cap)
 {
-    for (int d = cap; d >= 1; --d)
-        if (L % d == 0) return d;
-    return 1;
+    int d = 1;
+    while (2 * d <= cap && L % (2 * d) == 0) d *= 2;
+    return d;
 }
+
+static int log2i(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 TileShape default_tile(const int *Ls, int R, int model)
 {
@@ -153,8 +173,9 @@ TileShape default_tile(const int *Ls, int R, int model)
         }
         g = a;
     }
-    if (model == PYRO_ISING) return TileShape{divisor_at_most(g, 8), divisor_at_most(g, 8), divisor_at_most(g, 4)};
-    return TileShape{divisor_at_most(g, 8), divisor_at_most(g, 4), divisor_at_most(g, 4)};
+    if (model == PYRO_ISING)
+        return TileShape{pow2_divisor_at_most(g, 8), pow2_divisor_at_most(g, 8), pow2_divisor_at_most(g, 8)};
+    return TileShape{pow2_divisor_at_most(g, 8), pow2_divisor_at_most(g, 4), pow2_divisor_at_most(g, 4)};
 }
 
 size_t local_smem(int model, int prec, const TileShape &t)
@@ -164,7 +185,7 @@ size_t local_smem(int model, int prec, const TileShape &t)
 
 std::string check_tile(const int *Ls, int R, int model, int prec, const TileShape &t)
 {
-    if (t.TX < 1 || t.TY < 1 || t.TZ < 1) return "tile edges must be positive";
+    if (!is_pow2(t.TX) || !is_pow2(t.TY) || !is_pow2(t.TZ)) return "tile edges must be powers of two";
     for (int r = 0; r < R; ++r)
         if (Ls[r] % t.TX || Ls[r] % t.TY || Ls[r] % t.TZ) return "tile edges must divide every L";
     const int nt = t.TX * t.TY * t.TZ;
@@ -206,6 +227,9 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
     B.TX = t.TX;
     B.TY = t.TY;
     B.TZ = t.TZ;
+    B.lTX = log2i(t.TX);
+    B.lTY = log2i(t.TY);
+    B.lTZ = log2i(t.TZ);
     reps.assign(R, Rep{});
     ntiles = 0;
     nblocks = 0;
@@ -230,7 +254,7 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
             void **ptr;
             size_t bytes;
         } al[] = {{&p.spins, spin_bytes_of(model, prec, p.N)},
-                  {(void **)&p.P, (size_t)p.N * sizeof(int32_t)},
+                  {(void **)&p.P, (size_t)p.N * sizeof(unsigned long long)},
                   {(void **)&p.L16, (size_t)p.N * sizeof(uint16_t)},
                   {(void **)&p.F, (size_t)p.ncells * sizeof(uint16_t)},
                   {(void **)&p.dmask, (size_t)p.ncells * sizeof(uint32_t)},
@@ -244,11 +268,12 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
             owned.push_back(*a.ptr);
         }
         e = cudaMemsetAsync(p.st, 0, sizeof(DevStats), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p.P, 0xFF, (size_t)p.N * sizeof(unsigned long long), stream);
         if (e != cudaSuccess) return e;
     }
     B.tile_begin[R] = ntiles;
     B.block_begin[R] = nblocks;
-    e = cudaMalloc(&B.partials, (size_t)nblocks * 4 * sizeof(double));
+    e = cudaMalloc(&B.partials, (size_t)ntiles * 4 * sizeof(double));
     if (e != cudaSuccess) {
         err = "device allocation failed";
         return e;
@@ -303,16 +328,16 @@ cudaError_t Engine::set_beta(int r, double b)
 }
 
 // Phase p of a sweep: 0 tile-local labelling (with bond activation),
-// 1 crossing-root init, 2 crossing unions, 3 flip, 4 measurement,
-// 5 accumulation (mode as in accumulate_kernel).
+// 1 crossing unions, 2 flip, 3 measurement, 4 accumulation (mode as in
+// accumulate_kernel).
 void Engine::enqueue_phase(int p, int mode)
 {
-    if (p < 4) {
-        if (model == PYRO_ISING) ising_launch_phase(p, B, ntiles, nblocks, stream);
-        else vec_launch_phase(p, model, prec, B, ntiles, nblocks, stream);
-    } else if (p == 4) {
-        if (model == PYRO_ISING) ising_launch_measure(B, nblocks, stream);
-        else vec_launch_measure(model, prec, B, nblocks, stream);
+    if (p < 3) {
+        if (model == PYRO_ISING) ising_launch_phase(p, B, ntiles, stream);
+        else vec_launch_phase(p, model, prec, B, ntiles, stream);
+    } else if (p == 3) {
+        if (model == PYRO_ISING) ising_launch_measure(B, ntiles, stream);
+        else vec_launch_measure(model, prec, B, ntiles, stream);
     } else {
         if (model == PYRO_ISING) accumulate_kernel<true><<<R, 1024, 0, stream>>>(B, mode, 1);
         else accumulate_kernel<false><<<R, 1024, 0, stream>>>(B, mode, model);
@@ -327,8 +352,24 @@ void Engine::enqueue_sweeps(int n)
 
 void Engine::enqueue_measure(int mode)
 {
+    enqueue_phase(3, mode);
     enqueue_phase(4, mode);
-    enqueue_phase(5, mode);
+}
+
+// Crossing-cluster links are stamped with a per-sweep epoch (32 bits).
+// Before the epoch could wrap, every link array is reset to "no link" and
+// the epochs restart at 0.
+cudaError_t Engine::guard_epoch(int n)
+{
+    if (epoch + (uint64_t)n < 0xFFFFFFF0ull) return cudaSuccess;
+    for (auto &r : reps) {
+        const cudaError_t e = cudaMemsetAsync(r.P, 0xFF, (size_t)r.N * sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return e;
+    }
+    reset_epoch_kernel<<<1, MAX_REPS, 0, stream>>>(B);
+    launches += 1;
+    epoch = 0;
+    return cudaGetLastError();
 }
 
 cudaError_t Engine::compute_labels()
@@ -352,6 +393,11 @@ cudaError_t Engine::compute_labels()
 
 cudaError_t Engine::profile(int n, double *phase_ms)
 {
+    {
+        const cudaError_t e = guard_epoch(n);
+        if (e != cudaSuccess) return e;
+    }
+    epoch += (uint64_t)n;
     cudaEvent_t ev[NPHASE + 1];
     for (auto &x : ev)
         if (cudaEventCreate(&x) != cudaSuccess) return cudaGetLastError();
@@ -408,6 +454,11 @@ cudaGraphExec_t Engine::graph_for(int n)
 cudaError_t Engine::sweeps(int n)
 {
     if (n <= 0) return cudaSuccess;
+    {
+        const cudaError_t e = guard_epoch(n);
+        if (e != cudaSuccess) return e;
+    }
+    epoch += (uint64_t)n;
     if (use_graphs && own_stream) {
         const int chunk = n >= GRAPH_CHUNK ? GRAPH_CHUNK : 1;
         cudaGraphExec_t gk = graph_for(chunk);

@@ -10,9 +10,9 @@ namespace pyro {
 
 // Sweeps captured per CUDA graph for long runs.
 constexpr int GRAPH_CHUNK = 32;
-// Kernel launches (phases) per sweep: tile-local labelling, crossing-root
-// init, crossing unions, flip, measurement, accumulation.
-constexpr int NPHASE = 6;
+// Kernel launches (phases) per sweep: tile-local labelling, crossing
+// unions, flip, measurement, accumulation.
+constexpr int NPHASE = 5;
 
 struct GraphEntry {
     int n;
@@ -33,6 +33,7 @@ struct Engine {
     std::vector<void *> owned;
     std::vector<GraphEntry> graphs;
     uint64_t sweep = 0;
+    uint64_t epoch = 0;  // host mirror of the device epoch (same for all replicas)
     uint64_t launches = 0;
     bool labels_valid = false;
 
@@ -46,6 +47,7 @@ struct Engine {
     cudaError_t set_sweep(uint64_t s);
     cudaError_t set_trace(int r, int64_t cap);
     cudaError_t compute_labels();
+    cudaError_t guard_epoch(int n);
     int read_status(std::string &err);
     int launches_per_sweep() const;
 

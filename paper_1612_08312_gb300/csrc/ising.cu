@@ -2,27 +2,35 @@
 //
 // Spins are bit-packed, one uint16 per cubic cell (bit s of cell c is site
 // 16 c + s; 1 means s = -1).  Every kernel runs over a Batch of one or more
-// lattices.  The Ising-specific kernels:
+// lattices, one CTA per tile of TX x TY x TZ cells, one thread per cell.
 //
-//   ising_local     one CTA per tile of TX x TY x TZ cells, one thread per
-//                   cell.  Stages the tile's spin words plus a one-cell halo
-//                   on the backward faces in shared memory and draws the
-//                   random half-words of the satisfied bonds the cell owns:
-//                   a satisfied bond is active with p = 1 - exp(-2 beta J)
-//                   (SW bond activation).  Then the shared tile-local
-//                   labelling (sweep_core.cuh).
+//   ising_local     stages the tile's spin words plus a one-cell halo on the
+//                   backward faces, forms the 48 bonds' antiparallel bits by
+//                   shift-XOR, draws one Philox call per 16 bonds and
+//                   compares its bytes with the threshold four at a time
+//                   (a satisfied bond is active with p = 1 - exp(-2 beta J),
+//                   the SW bond rule), then runs the tile-local labelling.
 //   ising_flip      resolves every site to its cluster root and flips the
 //                   site iff the root's flip bit is set.
-//   ising_measure   counts antiparallel bonds and -1 spins per block (exact
+//   ising_measure   counts antiparallel bonds and -1 spins per tile (exact
 //                   integers; energy of Eq. 1, magnetisation of Eq. 2).
+//   boundary_kernel unites the clusters that cross tile faces (all models).
 //   labels_kernel   writes the canonical label of every site on demand.
 #include "sweep_core.cuh"
 
 namespace pyro {
 
-__host__ __device__ constexpr size_t ising_halo_bytes(int TX, int TY, int TZ)
+// Stage the tile's spin words and its backward halo into hs.
+__device__ __forceinline__ void stage_spin_halo(const TileCtx &c, const uint16_t *spins, uint16_t *hs)
 {
-    return (size_t)(TX + 1) * (TY + 1) * (TZ + 1) * sizeof(uint16_t);
+    const int nh = halo_cells(c.TX, c.TY, c.TZ);
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) hs[h] = spins[halo_cell(h, c.TX, c.TY, c.ox, c.oy, c.oz, c.L)];
+}
+
+__device__ __forceinline__ void cell_words(const TileCtx &c, const uint16_t *hs, uint32_t w[7])
+{
+#pragma unroll
+    for (int m = 0; m < 7; ++m) w[m] = hs[halo_index(c, m)];
 }
 
 __global__ void __launch_bounds__(512) ising_local_kernel(const __grid_constant__ Batch B)
@@ -31,72 +39,47 @@ __global__ void __launch_bounds__(512) ising_local_kernel(const __grid_constant_
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
-    const int nt = c.nt, L = c.L;
-    int *lab = smem;
-    uint32_t *plist = reinterpret_cast<uint32_t *>(smem + 16 * nt);
-    int *pcount = smem + 28 * nt;
-    uint16_t *hs = reinterpret_cast<uint16_t *>(smem + 28 * nt + 4);
-    const int HX = c.TX + 1, HY = c.TY + 1, HZ = c.TZ + 1;
-    const uint16_t *spins = static_cast<const uint16_t *>(R.spins);
+    const CoreSmem s = core_smem(smem, c.nt);
+    uint16_t *hs = reinterpret_cast<uint16_t *>(s.stage);
     const uint32_t sweep = (uint32_t)R.st->sweep;
     const uint64_t seed = R.seed;
-
-    for (int h = threadIdx.x; h < HX * HY * HZ; h += blockDim.x) {
-        const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-        int gx = c.ox + hx - 1, gy = c.oy + hy - 1, gz = c.oz + hz - 1;
-        gx += (gx < 0) ? L : 0;
-        gy += (gy < 0) ? L : 0;
-        gz += (gz < 0) ? L : 0;
-        hs[h] = spins[(int64_t)gx + (int64_t)L * ((int64_t)gy + (int64_t)L * gz)];
-    }
+    core_prologue(s);
+    stage_spin_halo(c, static_cast<const uint16_t *>(R.spins), hs);
     __syncthreads();
 
-    // spin words of this cell and its backward neighbours, by shift mask
     uint32_t w[7];
+    cell_words(c, hs, w);
+    uint32_t anti[3];
+    antiparallel_groups(w[0], down_word(w), anti[0], anti[1], anti[2]);
+    uint32_t act[3];
+    const ByteCompare bc(R.thr);
 #pragma unroll
-    for (int m = 0; m < 7; ++m)
-        w[m] = hs[(c.lx + 1 - (m & 1)) + HX * ((c.ly + 1 - ((m >> 1) & 1)) + HY * (c.lz + 1 - ((m >> 2) & 1)))];
-
-    uint64_t sat = 0;
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const int va = pair_a(k), vb = pair_b(k);
-            const uint32_t up = ((w[0] >> (4 * f + va)) ^ (w[0] >> (4 * f + vb))) & 1u;
-            const uint32_t dn = ((w[down_mask(f, va)] >> down_bit(f, va)) ^ (w[down_mask(f, vb)] >> down_bit(f, vb))) & 1u;
-            sat |= (uint64_t)(up ^ 1u) << (12 * f + k);
-            sat |= (uint64_t)(dn ^ 1u) << (12 * f + 6 + k);
-        }
-
-    // Bond 48 c + j (j = 0..47) compares half j & 7 of BOND call 6 c + j / 8
-    // (low half from TIE call 6 c + j / 8 on a tie) with the threshold.
-    uint64_t act = 0;
-    const HalfCompare hc(R.thr);
-    if (hc.all) {
-        act = sat;
-    } else if (R.thr > 0) {
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const uint32_t byte = (uint32_t)(sat >> (8 * q)) & 0xFFu;
-            if (!byte) continue;
-            const uint64_t j = 6 * (uint64_t)c.cell + q;
-            const uint4 wd = philox_call(seed, sweep, TAG_BOND, j);
+    for (int g = 0; g < 3; ++g) {
+        const uint32_t sat = ~anti[g] & 0xFFFFu;
+        uint32_t a = 0;
+        if (bc.all) {
+            a = sat;
+        } else if (!bc.none && sat) {
+            // bond 48 c + 16 g + 4 f + q: byte 4 f + q of BOND call 3 c + g
+            const uint4 wd = philox_call(seed, sweep, TAG_BOND, 3 * (uint64_t)c.cell + g);
             const uint32_t ww[4] = {wd.x, wd.y, wd.z, wd.w};
+            const uint32_t t4 = bc.t8 * 0x01010101u;
 #pragma unroll
-            for (int h = 0; h < 8; ++h) {
-                if (!((byte >> h) & 1u)) continue;
-                const uint32_t hi = (ww[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
-                bool a = hi < hc.thi;
-                if (hi == hc.thi) {
-                    const uint4 wt = philox_call(seed, sweep, TAG_TIE, j);
-                    a = ((word_of(wt, h >> 1) >> (16 * (h & 1))) & 0xFFFFu) < hc.tlo;
+            for (int f = 0; f < 4; ++f) {
+                uint32_t nib = byte_flags_to_nibble(bytes_lt(ww[f], t4));
+                uint32_t tie = byte_flags_to_nibble(bytes_eq(ww[f], t4)) & (sat >> (4 * f));
+                while (tie) {  // top bytes equal: compare the low 24 bits
+                    const int q = __ffs(tie) - 1;
+                    tie &= tie - 1;
+                    if (tie_bits(seed, sweep, c.cell, g, f, q) < bc.t24) nib |= 1u << q;
                 }
-                act |= (uint64_t)(a ? 1u : 0u) << (8 * q + h);
+                a |= nib << (4 * f);
             }
+            a &= sat;
         }
+        act[g] = a;
     }
-    local_core(c, R, act, sweep, lab, plist, pcount);
+    local_core(c, R, s, act[0], act[1], act[2], sweep);
 }
 
 __global__ void __launch_bounds__(512) ising_flip_kernel(const __grid_constant__ Batch B)
@@ -105,11 +88,9 @@ __global__ void __launch_bounds__(512) ising_flip_kernel(const __grid_constant__
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
-    uint16_t *ls = reinterpret_cast<uint16_t *>(smem);
-    uint16_t *fs = ls + 16 * c.nt;
     int root[16];
     uint32_t flip;
-    resolve_cell(c, R, ls, fs, root, flip);
+    resolve_cell(c, R, smem, (uint32_t)R.st->epoch, root, flip);
     uint16_t *spins = static_cast<uint16_t *>(R.spins);
     spins[c.cell] = (uint16_t)((uint32_t)spins[c.cell] ^ flip);
 }
@@ -121,54 +102,33 @@ __global__ void __launch_bounds__(512) labels_kernel(const __grid_constant__ Bat
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
-    uint16_t *ls = reinterpret_cast<uint16_t *>(smem);
-    uint16_t *fs = ls + 16 * c.nt;
     int root[16];
     uint32_t flip;
-    resolve_cell(c, R, ls, fs, root, flip);
+    resolve_cell(c, R, smem, (uint32_t)R.st->last_epoch, root, flip);
     int4 *dst = reinterpret_cast<int4 *>(R.labels + 16 * c.cell);
 #pragma unroll
     for (int q = 0; q < 4; ++q) dst[q] = make_int4(root[4 * q], root[4 * q + 1], root[4 * q + 2], root[4 * q + 3]);
 }
 
-// Antiparallel bonds (48 per cell) and -1 spins, exact integer counts per
-// block of CELL_BLOCK cells.
-__global__ void __launch_bounds__(CELL_BLOCK) ising_measure_kernel(const __grid_constant__ Batch B)
+// Antiparallel bonds (48 per cell) and -1 spins: exact integer counts per
+// tile, written to the tile's partial slot.
+__global__ void __launch_bounds__(512) ising_measure_kernel(const __grid_constant__ Batch B)
 {
-    const int r = find_rep(B.block_begin, B.R, blockIdx.x);
+    extern __shared__ __align__(16) int smem[];
+    const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
-    const int64_t cell = (blockIdx.x - B.block_begin[r]) * CELL_BLOCK + threadIdx.x;
-    unsigned long long anti = 0, ndown = 0;
-    if (cell < R.ncells) {
-        const int L = R.L;
-        const uint16_t *spins = static_cast<const uint16_t *>(R.spins);
-        const int x = (int)(cell % L), y = (int)((cell / L) % L), z = (int)(cell / ((int64_t)L * L));
-        uint32_t w[7];
-#pragma unroll
-        for (int m = 0; m < 7; ++m) {
-            const int cx = (m & 1) ? wrap_back(x, L) : x;
-            const int cy = (m & 2) ? wrap_back(y, L) : y;
-            const int cz = (m & 4) ? wrap_back(z, L) : z;
-            w[m] = spins[(int64_t)cx + (int64_t)L * ((int64_t)cy + (int64_t)L * cz)];
-        }
-        uint32_t a = 0;
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const int va = pair_a(k), vb = pair_b(k);
-                a += ((w[0] >> (4 * f + va)) ^ (w[0] >> (4 * f + vb))) & 1u;
-                a += ((w[down_mask(f, va)] >> down_bit(f, va)) ^ (w[down_mask(f, vb)] >> down_bit(f, vb))) & 1u;
-            }
-        anti = a;
-        ndown = __popc(w[0]);
-    }
-    __shared__ unsigned long long red[2][CELL_BLOCK / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        anti += __shfl_xor_sync(0xffffffffu, anti, o);
-        ndown += __shfl_xor_sync(0xffffffffu, ndown, o);
-    }
+    const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
+    uint16_t *hs = reinterpret_cast<uint16_t *>(smem);
+    stage_spin_halo(c, static_cast<const uint16_t *>(R.spins), hs);
+    __syncthreads();
+    uint32_t w[7];
+    cell_words(c, hs, w);
+    uint32_t A, Bg, C;
+    antiparallel_groups(w[0], down_word(w), A, Bg, C);
+    const unsigned mask = lanes_mask(c.nt);
+    const unsigned anti = __reduce_add_sync(mask, (unsigned)(__popc(A) + __popc(Bg) + __popc(C)));
+    const unsigned ndown = __reduce_add_sync(mask, (unsigned)__popc(w[0]));
+    __shared__ unsigned red[2][16];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][wid] = anti;
@@ -177,7 +137,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) ising_measure_kernel(const __grid_
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long sa = 0, sd = 0;
-        for (int q = 0; q < CELL_BLOCK / 32; ++q) {
+        for (int q = 0; q < (c.nt + 31) / 32; ++q) {
             sa += red[0][q];
             sd += red[1][q];
         }
@@ -203,12 +163,48 @@ __global__ void __launch_bounds__(CELL_BLOCK) ising_init_kernel(const __grid_con
     static_cast<uint16_t *>(R.spins)[cell] = (uint16_t)word;
 }
 
-// ------------------------------------------------------------ launchers --
-size_t ising_local_smem(const TileShape &t)
+// Unite the clusters joined by the union pairs that leave each tile, and
+// mark both tile-local roots as crossing (bit 15 of their L16 entry).
+// Model-independent: used by the n-vector sweeps too.
+__global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ Batch B)
 {
-    const int nt = t.TX * t.TY * t.TZ;
-    return core_smem_bytes(nt) + ising_halo_bytes(t.TX, t.TY, t.TZ);
+    const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
+    const Rep &R = B.reps[r];
+    const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
+    if (!(c.lx == 0 || c.ly == 0 || c.lz == 0)) return;
+    uint32_t todo = R.dmask[c.cell];
+    if (!todo) return;
+    const int L = c.L;
+    const int x = c.ox + c.lx, y = c.oy + c.ly, z = c.oz + c.lz;
+    const uint32_t stamp = (uint32_t)R.st->epoch;
+    unsigned long long *P = R.P;
+    unsigned *Lw = reinterpret_cast<unsigned *>(R.L16);
+    bool ok = true;
+    while (todo) {
+        const int bit = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int f = bit / 6, k = bit % 6;
+        int g[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int v = e == 0 ? pair_a(k) : pair_b(k);
+            const int m = down_mask(f, v);
+            const int cx = (m & 1) ? wrap_back(x, L) : x;
+            const int cy = (m & 2) ? wrap_back(y, L) : y;
+            const int cz = (m & 4) ? wrap_back(z, L) : z;
+            g[e] = crossing_root(R, B, cx, cy, cz, down_bit(f, v));
+            const unsigned bitm = 1u << (15 + 16 * (g[e] & 1));
+            if (!(__ldcg(Lw + (g[e] >> 1)) & bitm)) atomicOr(Lw + (g[e] >> 1), bitm);
+        }
+        ok &= punite(P, g[0], g[1], stamp);
+    }
+    if (!ok) atomicOr(&R.st->status, ST_NOCONVERGE);
 }
+
+// ------------------------------------------------------------ launchers --
+static size_t halo_spin_bytes(const TileShape &t) { return (size_t)halo_cells(t.TX, t.TY, t.TZ) * sizeof(uint16_t); }
+
+size_t ising_local_smem(const TileShape &t) { return core_smem_bytes(t.TX * t.TY * t.TZ) + halo_spin_bytes(t); }
 
 size_t resolve_smem(const TileShape &t) { return resolve_smem_bytes(t.TX * t.TY * t.TZ); }
 
@@ -228,11 +224,9 @@ void ising_launch_init(const Batch &B, int64_t nblocks, int random, cudaStream_t
     ising_init_kernel<<<(unsigned)nblocks, CELL_BLOCK, 0, s>>>(B, random);
 }
 
-void launch_boundary(int unite, const Batch &B, int64_t ntiles, cudaStream_t s)
+void launch_boundary(const Batch &B, int64_t ntiles, cudaStream_t s)
 {
-    const int nt = B.TX * B.TY * B.TZ;
-    if (unite) boundary_kernel<true><<<(unsigned)ntiles, nt, 0, s>>>(B);
-    else boundary_kernel<false><<<(unsigned)ntiles, nt, 0, s>>>(B);
+    boundary_kernel<<<(unsigned)ntiles, B.TX * B.TY * B.TZ, 0, s>>>(B);
 }
 
 void launch_labels(const Batch &B, int64_t ntiles, cudaStream_t s)
@@ -241,21 +235,20 @@ void launch_labels(const Batch &B, int64_t ntiles, cudaStream_t s)
     labels_kernel<<<(unsigned)ntiles, B.TX * B.TY * B.TZ, resolve_smem(t), s>>>(B);
 }
 
-// Phase p of a sweep: 0 local labelling, 1 boundary init, 2 boundary unite,
-// 3 flip.
-void ising_launch_phase(int p, const Batch &B, int64_t ntiles, int64_t nblocks, cudaStream_t s)
+// Phase p of a sweep: 0 local labelling, 1 crossing unions, 2 flip.
+void ising_launch_phase(int p, const Batch &B, int64_t ntiles, cudaStream_t s)
 {
     const TileShape t{B.TX, B.TY, B.TZ};
     const int nt = B.TX * B.TY * B.TZ;
     if (p == 0) ising_local_kernel<<<(unsigned)ntiles, nt, ising_local_smem(t), s>>>(B);
-    else if (p == 1 || p == 2) launch_boundary(p == 2, B, ntiles, s);
+    else if (p == 1) launch_boundary(B, ntiles, s);
     else ising_flip_kernel<<<(unsigned)ntiles, nt, resolve_smem(t), s>>>(B);
-    (void)nblocks;
 }
 
-void ising_launch_measure(const Batch &B, int64_t nblocks, cudaStream_t s)
+void ising_launch_measure(const Batch &B, int64_t ntiles, cudaStream_t s)
 {
-    ising_measure_kernel<<<(unsigned)nblocks, CELL_BLOCK, 0, s>>>(B);
+    const TileShape t{B.TX, B.TY, B.TZ};
+    ising_measure_kernel<<<(unsigned)ntiles, B.TX * B.TY * B.TZ, halo_spin_bytes(t), s>>>(B);
 }
 
 }  // namespace pyro

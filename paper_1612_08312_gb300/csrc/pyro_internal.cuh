@@ -95,6 +95,8 @@ __host__ __device__ constexpr int pair_b(int k) { return k < 3 ? k + 1 : (k < 5 
 // ------------------------------------------------------------- contexts --
 struct DevStats {
     unsigned long long sweep;  // sweep field of the next sweep's Philox counters
+    unsigned long long epoch;       // stamp of the next sweep's crossing-cluster links
+    unsigned long long last_epoch;  // stamp of the last completed sweep's links
     int status;                // ST_* bits
     int pad;
     // accumulators (Neumaier): E, E^2, m^2, m^4, |m|
@@ -114,7 +116,7 @@ struct Rep {
     void *spins;       // Ising: uint16 per cell; n-vector: n planes of N values
     uint16_t *L16;     // per site: tile-local index of its tile-local root;
                        // bit 15 set on a root whose cluster crosses a tile face
-    int32_t *P;        // global union-find parents, used at crossing roots only
+    unsigned long long *P;  // crossing-cluster links: (epoch stamp << 32) | parent
     uint16_t *F;       // the sweep's flip bit of every site, one word per cell
     uint32_t *dmask;   // union pairs of face cells that cross the tile (24 bits)
     int32_t *labels;   // canonical labels (filled on demand), or NULL
@@ -131,14 +133,16 @@ struct Rep {
 
 // Up to MAX_REPS lattices updated by one launch per phase.  Blocks of the
 // tiled kernels map to (replica, tile) through tile_begin; blocks of the
-// per-cell kernels (256 cells each) through block_begin.
+// per-cell kernels (256 cells each) through block_begin.  Tile edges are
+// powers of two that divide every replica's L.
 constexpr int MAX_REPS = 64;
 constexpr int CELL_BLOCK = 256;
 
 struct Batch {
     const Rep *reps;
-    double *partials;  // 4 per per-cell block
+    double *partials;  // 4 per tile
     int R, TX, TY, TZ;
+    int lTX, lTY, lTZ;  // log2 of the (power-of-two) tile edges
     int64_t tile_begin[MAX_REPS + 1];
     int64_t block_begin[MAX_REPS + 1];
 };

@@ -3,9 +3,16 @@
 // tile-crossing clusters, and the resolution of every site to its cluster's
 // canonical root.
 //
-// Bond bits of a cell: bit 12 f + k is bond k of FCC point f (k = 0..5 its
-// "up" tetrahedron, k = 6..11 the "down" tetrahedron through site (f, 0)).
-// Site bits: s = 4 f + mu.  Bond b = 48 c + 12 f + k of cell c.
+// Bonds of a cell.  Each of the cell's four FCC points f owns an "up"
+// tetrahedron (its sites 4 f .. 4 f + 3) and a "down" tetrahedron (its
+// site 4 f and three sites of backward neighbour cells).  The 48 bonds are
+// kept as three 16-bit groups, bit 4 f + q of group g:
+//   g = 0 (A): up pairs    q = 0 (0,1)  1 (1,2)  2 (2,3)  3 (0,3)
+//   g = 1 (B): up (0,2), up (1,3), down (0,2), down (1,3)
+//   g = 2 (C): down pairs  q = 0 (0,1)  1 (1,2)  2 (2,3)  3 (0,3)
+// so that shift-XOR of a 16-bit spin word yields four bonds at once, and
+// the bond with random-number id b = 48 c + 16 g + 4 f + q draws the top
+// byte of its uniform from byte (b & 15) of BOND call b >> 4 = 3 c + g.
 #pragma once
 
 #include "ccl.cuh"
@@ -13,8 +20,9 @@
 namespace pyro {
 
 // Position of the calling thread's cell in its tile and in the lattice.
+// Tile edges are powers of two (shifts, no divisions).
 struct TileCtx {
-    int TX, TY, TZ, nt, L;
+    int TX, TY, TZ, lTX, lTY, nt, L;
     int ox, oy, oz;
     int lx, ly, lz, t;
     int64_t cell;
@@ -30,15 +38,18 @@ __device__ __forceinline__ TileCtx tile_ctx(const Batch &B, const Rep &R, int64_
     c.TX = B.TX;
     c.TY = B.TY;
     c.TZ = B.TZ;
+    c.lTX = B.lTX;
+    c.lTY = B.lTY;
     c.nt = B.TX * B.TY * B.TZ;
     c.L = R.L;
-    c.ox = (int)(tile % R.ntx) * c.TX;
-    c.oy = (int)((tile / R.ntx) % R.nty) * c.TY;
-    c.oz = (int)(tile / ((int64_t)R.ntx * R.nty)) * c.TZ;
+    const int64_t txy = tile / R.ntx;
+    c.ox = (int)(tile - txy * R.ntx) * c.TX;
+    c.oy = (int)(txy % R.nty) * c.TY;
+    c.oz = (int)(txy / R.nty) * c.TZ;
     c.t = threadIdx.x;
-    c.lx = c.t % c.TX;
-    c.ly = (c.t / c.TX) % c.TY;
-    c.lz = c.t / (c.TX * c.TY);
+    c.lx = c.t & (c.TX - 1);
+    c.ly = (c.t >> c.lTX) & (c.TY - 1);
+    c.lz = c.t >> (c.lTX + c.lTY);
     const int x = c.ox + c.lx, y = c.oy + c.ly, z = c.oz + c.lz;
     c.cell = (int64_t)x + (int64_t)c.L * ((int64_t)y + (int64_t)c.L * z);
     // a tile that spans a whole axis wraps onto itself along it
@@ -49,6 +60,31 @@ __device__ __forceinline__ TileCtx tile_ctx(const Batch &B, const Rep &R, int64_
     c.dym = c.ly > 0 ? -c.TX : (c.TY - 1) * c.TX;
     c.dzm = c.lz > 0 ? -c.TX * c.TY : (c.TZ - 1) * c.TX * c.TY;
     return c;
+}
+
+// Lanes of the calling thread's warp that exist in a block of nt threads.
+__device__ __forceinline__ unsigned lanes_mask(int nt)
+{
+    const int cnt = min(32, nt - (int)(threadIdx.x & ~31u));
+    return cnt >= 32 ? 0xffffffffu : ((1u << cnt) - 1u);
+}
+
+// Deterministic sum over the block's nt threads (fixed tree in shared
+// memory, any nt); result valid in thread 0.  scratch holds nt doubles.
+__device__ __forceinline__ double tile_sum_f64(double v, int nt, double *scratch)
+{
+    const int t = threadIdx.x;
+    scratch[t] = v;
+    __syncthreads();
+    int span = 1;
+    while (span < nt) span <<= 1;
+    for (int o = span >> 1; o > 0; o >>= 1) {
+        if (t < o && t + o < nt) scratch[t] = __dadd_rn(scratch[t], scratch[t + o]);
+        __syncthreads();
+    }
+    const double r = scratch[0];
+    __syncthreads();
+    return r;
 }
 
 // Tile-local cell of a vertex whose cell is this cell stepped back along
@@ -65,34 +101,134 @@ __device__ __forceinline__ bool vertex_inside(const TileCtx &c, int m)
 
 __device__ __forceinline__ int wrap_back(int v, int L) { return v == 0 ? L - 1 : v - 1; }
 
-// Global site index of vertex v of the down tetrahedron of FCC point f of
-// cell (x, y, z).
-__device__ __forceinline__ int down_vertex_global(int x, int y, int z, int L, int f, int v)
+// Cells of the backward halo staged by the tile kernels.
+__host__ __device__ constexpr int halo_cells(int TX, int TY, int TZ) { return (TX + 1) * (TY + 1) * (TZ + 1); }
+
+__device__ __forceinline__ int halo_index(const TileCtx &c, int m)
 {
-    const int m = down_mask(f, v);
-    const int cx = (m & 1) ? wrap_back(x, L) : x;
-    const int cy = (m & 2) ? wrap_back(y, L) : y;
-    const int cz = (m & 4) ? wrap_back(z, L) : z;
-    return 16 * (cx + L * (cy + L * cz)) + down_bit(f, v);
+    const int HX = c.TX + 1, HY = c.TY + 1;
+    return (c.lx + 1 - (m & 1)) + HX * ((c.ly + 1 - ((m >> 1) & 1)) + HY * (c.lz + 1 - ((m >> 2) & 1)));
 }
 
-// The 16 flip bits of cell c: bits 16 c .. 16 c + 15 of the FLIP stream
-// (bit i = bit i & 127 of call i >> 7).  One Philox call serves 8 cells;
-// when the 8 cells are 8 consecutive lanes (TX a multiple of 8) the lane
-// with lx % 8 == 0 draws it and shares it.
-__device__ __forceinline__ uint32_t cell_flip_bits(const TileCtx &c, uint64_t seed, uint32_t sweep, uint32_t tag,
-                                                   bool share)
+// Global cell of halo entry h of the tile with origin (ox, oy, oz).
+__device__ __forceinline__ int64_t halo_cell(int h, int TX, int TY, int ox, int oy, int oz, int L)
+{
+    const int HX = TX + 1, HY = TY + 1;
+    const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+    int gx = ox + hx - 1, gy = oy + hy - 1, gz = oz + hz - 1;
+    gx += (gx < 0) ? L : 0;
+    gy += (gy < 0) ? L : 0;
+    gz += (gz < 0) ? L : 0;
+    return (int64_t)gx + (int64_t)L * ((int64_t)gy + (int64_t)L * gz);
+}
+
+// ------------------------------------------------------ bond bit layout --
+// Vertex pair of slot q of group g (see the header comment); up = whether
+// the pair belongs to the up tetrahedron.
+__host__ __device__ constexpr int slot_a(int g, int q) { return g == 1 ? (q & 1) : (q == 3 ? 0 : q); }
+__host__ __device__ constexpr int slot_b(int g, int q) { return g == 1 ? (q & 1) + 2 : (q == 3 ? 3 : q + 1); }
+__host__ __device__ constexpr bool slot_up(int g, int q) { return g == 0 || (g == 1 && q < 2); }
+
+// Index into the tetrahedron table from a tetrahedron's bond bits: bits
+// 0..3 pairs (0,1) (1,2) (2,3) (0,3), bits 4..5 pairs (0,2) (1,3).
+__device__ __forceinline__ uint32_t up_tet_index(uint32_t A, uint32_t Bg, int f)
+{
+    return ((A >> (4 * f)) & 0xFu) | (((Bg >> (4 * f)) & 0x3u) << 4);
+}
+__device__ __forceinline__ uint32_t down_tet_index(uint32_t C, uint32_t Bg, int f)
+{
+    return ((C >> (4 * f)) & 0xFu) | (((Bg >> (4 * f + 2)) & 0x3u) << 4);
+}
+
+// Table entry of a tetrahedron with bond bits `idx` (order as above):
+// 2 bits per vertex v = the smallest vertex connected to v.
+__device__ __forceinline__ uint32_t tet_table_entry(uint32_t idx)
+{
+    int rr[4] = {0, 1, 2, 3};
+    const int pa[6] = {0, 1, 2, 0, 0, 1};
+    const int pb[6] = {1, 2, 3, 3, 2, 3};
+#pragma unroll
+    for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if ((idx >> k) & 1u) {
+                const int m = min(rr[pa[k]], rr[pb[k]]);
+                rr[pa[k]] = m;
+                rr[pb[k]] = m;
+            }
+    return (uint32_t)(rr[0] | (rr[1] << 2) | (rr[2] << 4) | (rr[3] << 6));
+}
+
+// The four spins of the down tetrahedron of each FCC point f of a cell,
+// gathered into one 16-bit word (bit 4 f + v = vertex v).  w[m] = spin word
+// of the cell stepped back along the axes of mask m.
+__device__ __forceinline__ uint32_t down_word(const uint32_t w[7])
+{
+    uint32_t D = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) D |= ((w[down_mask(f, v)] >> down_bit(f, v)) & 1u) << (4 * f + v);
+    return D;
+}
+
+// Antiparallel bits of the three bond groups from the up and down spin
+// words (shift-XOR within each nibble).
+__device__ __forceinline__ void antiparallel_groups(uint32_t U, uint32_t D, uint32_t &A, uint32_t &Bg, uint32_t &C)
+{
+    const uint32_t u1 = U ^ (U >> 1), u2 = U ^ (U >> 2), u3 = U ^ (U >> 3);
+    const uint32_t d1 = D ^ (D >> 1), d2 = D ^ (D >> 2), d3 = D ^ (D >> 3);
+    A = (u1 & 0x7777u) | ((u3 & 0x1111u) << 3);
+    Bg = (u2 & 0x3333u) | ((d2 & 0x3333u) << 2);
+    C = (d1 & 0x7777u) | ((d3 & 0x1111u) << 3);
+}
+
+// Bytewise unsigned a < b: bit 7 of each byte of the result.
+__device__ __forceinline__ uint32_t bytes_lt(uint32_t a, uint32_t b)
+{
+    const uint32_t d = (a | 0x80808080u) - (b & 0x7F7F7F7Fu);  // bit 7: low 7 bits of a >= those of b
+    return ((~(a ^ b) & ~d) | (~a & b)) & 0x80808080u;
+}
+
+// Bytewise a == b: bit 7 of each byte.
+__device__ __forceinline__ uint32_t bytes_eq(uint32_t a, uint32_t b)
+{
+    const uint32_t t = a ^ b;
+    return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
+}
+
+// Bit 7 of the four bytes -> four low bits.
+__device__ __forceinline__ uint32_t byte_flags_to_nibble(uint32_t f) { return (((f >> 7) * 0x204081u) >> 21) & 0xFu; }
+
+// Threshold of a bond: active iff its 32-bit uniform w < thr (thr <= 2^32).
+// w's top byte comes from the BOND stream, its low 24 bits (only needed on
+// a tie of the top bytes) from the TIE stream.
+struct ByteCompare {
+    uint32_t t8, t24;
+    bool all, none;
+    __device__ __forceinline__ explicit ByteCompare(uint64_t thr)
+        : t8((uint32_t)(thr >> 24)), t24((uint32_t)(thr & 0xFFFFFFu)), all(thr >= (1ull << 32)), none(thr == 0) {}
+};
+
+// Low 24 bits of the TIE-stream word of bond id 48 c + 16 g + 4 f + q.
+__device__ __forceinline__ uint32_t tie_bits(uint64_t seed, uint32_t sweep, int64_t cell, int g, int f, int q)
+{
+    const uint4 w = philox_call(seed, sweep, TAG_TIE, 12 * (uint64_t)cell + 4 * g + f);
+    return word_of(w, q) & 0xFFFFFFu;
+}
+
+// The cell's 16 flip bits: bits 16 c .. 16 c + 15 of the FLIP stream (bit i
+// = bit i & 127 of call i >> 7).  One Philox call serves 8 cells; when the
+// 8 cells are 8 consecutive lanes (TX a multiple of 8) one lane draws it.
+__device__ __forceinline__ uint32_t cell_flip_bits(const TileCtx &c, uint64_t seed, uint32_t sweep)
 {
     const uint64_t j = (uint64_t)c.cell >> 3;
-    uint32_t word;
     const int wsel = (int)((c.cell & 7) >> 1);
-    if (share) {
-        // lanes present in this (possibly partial) warp of the block
-        const int wbase = threadIdx.x & ~31;
-        const int cnt = min(32, c.nt - wbase);
-        const unsigned mask = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
+    uint32_t word;
+    if ((c.TX & 7) == 0) {
+        const unsigned mask = lanes_mask(c.nt);
         uint4 w = make_uint4(0, 0, 0, 0);
-        if ((c.lx & 7) == 0) w = philox_call(seed, sweep, tag, j);
+        if ((c.lx & 7) == 0) w = philox_call(seed, sweep, TAG_FLIP, j);
         const int leader = (threadIdx.x & 31) & ~7;
         w.x = __shfl_sync(mask, w.x, leader);
         w.y = __shfl_sync(mask, w.y, leader);
@@ -100,63 +236,82 @@ __device__ __forceinline__ uint32_t cell_flip_bits(const TileCtx &c, uint64_t se
         w.w = __shfl_sync(mask, w.w, leader);
         word = word_of(w, wsel);
     } else {
-        word = word_of(philox_call(seed, sweep, tag, j), wsel);
+        word = word_of(philox_call(seed, sweep, TAG_FLIP, j), wsel);
     }
     return (word >> (16 * (int)(c.cell & 1))) & 0xFFFFu;
 }
 
-// Bond decision from a 32-bit uniform assembled lazily: high half from the
-// BOND call, low half (from the TIE call) only when the high halves tie.
-// thr <= 2^32; the bond is active iff w < thr.
-struct HalfCompare {
-    uint32_t thi, tlo;
-    bool all;
-    __device__ __forceinline__ explicit HalfCompare(uint64_t thr)
-        : thi((uint32_t)(thr >> 16)), tlo((uint32_t)(thr & 0xFFFFu)), all(thr >= (1ull << 32)) {}
+// --------------------------------------------------- tile-local labelling --
+// Shared memory of the local kernels: labels (16 nt ints), union pairs
+// (12 nt words), pair counter, tetrahedron table (64 bytes); the model's
+// staging area follows.
+__host__ __device__ constexpr size_t core_smem_bytes(int nt) { return (size_t)28 * nt * 4 + 16 + 64; }
+
+struct CoreSmem {
+    int *lab;
+    uint32_t *plist;
+    int *pcount;
+    uint8_t *lut;
+    unsigned char *stage;  // model staging area (16-byte aligned)
 };
 
-// Shared-memory layout of the tile-local labelling, after the model's own
-// staging area: labels (16 nt ints), the union-pair list (12 nt words) and
-// its counter.
-__host__ __device__ constexpr size_t core_smem_bytes(int nt) { return (size_t)16 * nt * 4 + (size_t)12 * nt * 4 + 16; }
+__device__ __forceinline__ CoreSmem core_smem(int *smem, int nt)
+{
+    CoreSmem s;
+    s.lab = smem;
+    s.plist = reinterpret_cast<uint32_t *>(smem + 16 * nt);
+    s.pcount = smem + 28 * nt;
+    s.lut = reinterpret_cast<uint8_t *>(smem + 28 * nt + 4);
+    s.stage = reinterpret_cast<unsigned char *>(smem + 28 * nt + 20);
+    return s;
+}
 
-// Tile-local labelling of one cell's sites given its 48 active-bond bits.
+// Called by every thread before the model's staging (covered by the same
+// __syncthreads): clears the pair counter and fills the table.
+__device__ __forceinline__ void core_prologue(const CoreSmem &s)
+{
+    if (threadIdx.x == 0) *s.pcount = 0;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) s.lut[i] = (uint8_t)tet_table_entry((uint32_t)i);
+}
+
+// Tile-local labelling of one cell's sites from its active-bond groups.
 // Writes L16 (tile-local root of each site), F (flip bits) and, for face
-// cells, dmask (union pairs leaving the tile).  Called by every thread of
-// the block.
-__device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, uint64_t act, uint32_t sweep,
-                                           int *lab, uint32_t *plist, int *pcount)
+// cells, dmask (the union pairs that leave the tile: bit 6 f + k, k the
+// pair index of (a, b) in the order (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)).
+// Called by every thread of the block after the staging barrier.
+__device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const CoreSmem &s, uint32_t A, uint32_t Bg,
+                                           uint32_t C, uint32_t sweep)
 {
     const int nt = c.nt;
-    if (threadIdx.x == 0) *pcount = 0;
-    // up tetrahedra: component minima in registers
+    uint32_t uptab[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        int rr[4];
-        tet_components((uint32_t)(act >> (12 * f)) & 63u, rr);
+        uptab[f] = s.lut[up_tet_index(A, Bg, f)];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) lab[lslot(16 * c.t + 4 * f + v, nt)] = 16 * c.t + 4 * f + rr[v];
+        for (int v = 0; v < 4; ++v)
+            s.lab[lslot(16 * c.t + 4 * f + v, nt)] = 16 * c.t + 4 * f + (int)((uptab[f] >> (2 * v)) & 3u);
     }
-    // down tetrahedra: union pairs (v, smallest vertex of v's component)
     uint32_t inpairs = 0, cross = 0;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        int rr[4];
-        tet_components((uint32_t)(act >> (12 * f + 6)) & 63u, rr);
+        const uint32_t dt = s.lut[down_tet_index(C, Bg, f)];
 #pragma unroll
         for (int v = 1; v < 4; ++v) {
-            if (rr[v] == v) continue;
-            const int k = pair_index(rr[v], v);
-            const bool inside = vertex_inside(c, down_mask(f, rr[v])) && vertex_inside(c, down_mask(f, v));
+            const int rv = (int)((dt >> (2 * v)) & 3u);
+            if (rv == v) continue;
+            const int k = pair_index(rv, v);
+            // rv < v; both vertices of the pair must lie in the tile
+            bool inside = vertex_inside(c, down_mask(f, v));
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+                if (rv == u) inside = inside && vertex_inside(c, down_mask(f, u));
             if (inside) inpairs |= 1u << (6 * f + k);
             else cross |= 1u << (6 * f + k);
         }
     }
-    __syncthreads();  // labels initialised, counter cleared
-    // append this cell's in-tile pairs to the block's list (the order of the
-    // list does not change the final roots: they are cluster minima)
+    __syncthreads();  // labels initialised
     const int n = __popc(inpairs);
-    int base = n ? atomicAdd(pcount, n) : 0;
+    int base = n ? atomicAdd(s.pcount, n) : 0;
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
@@ -165,121 +320,162 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, uint6
                 const int va = pair_a(k), vb = pair_b(k);
                 const int a = 16 * vertex_local_cell(c, down_mask(f, va)) + down_bit(f, va);
                 const int b = 16 * vertex_local_cell(c, down_mask(f, vb)) + down_bit(f, vb);
-                plist[base++] = (uint32_t)a | ((uint32_t)b << 16);
+                s.plist[base++] = (uint32_t)a | ((uint32_t)b << 16);
             }
     __syncthreads();
-    const int np = *pcount;
+    const int np = *s.pcount;
     bool ok = true;
     for (int e = threadIdx.x; e < np; e += nt) {
-        const uint32_t pr = plist[e];
-        ok &= sunite(lab, (int)(pr & 0xFFFFu), (int)(pr >> 16), nt);
+        const uint32_t pr = s.plist[e];
+        ok &= sunite(s.lab, (int)(pr & 0xFFFFu), (int)(pr >> 16), nt);
     }
     if (!ok) atomicOr(&R.st->status, ST_NOCONVERGE);
     __syncthreads();
-    // resolve to tile-local roots
+    // resolve: one find per up-tetrahedron component, shared by its sites
     uint32_t packed[8];
 #pragma unroll
-    for (int s = 0; s < 16; s += 2) {
-        const uint32_t r0 = (uint32_t)sfind(lab, 16 * c.t + s, nt);
-        const uint32_t r1 = (uint32_t)sfind(lab, 16 * c.t + s + 1, nt);
-        packed[s >> 1] = r0 | (r1 << 16);
+    for (int f = 0; f < 4; ++f) {
+        uint32_t root[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const uint32_t rv = (uptab[f] >> (2 * v)) & 3u;
+            uint32_t r = 0;
+#pragma unroll
+            for (int u = 0; u < v; ++u)
+                if (rv == (uint32_t)u) r = root[u];
+            if (rv == (uint32_t)v) r = (uint32_t)sfind(s.lab, 16 * c.t + 4 * f + v, nt);
+            root[v] = r;
+        }
+        packed[2 * f] = root[0] | (root[1] << 16);
+        packed[2 * f + 1] = root[2] | (root[3] << 16);
     }
     uint4 *dst = reinterpret_cast<uint4 *>(R.L16 + 16 * c.cell);
     dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-    R.F[c.cell] = (uint16_t)cell_flip_bits(c, R.seed, sweep, TAG_FLIP, (c.TX & 7) == 0);
+    R.F[c.cell] = (uint16_t)cell_flip_bits(c, R.seed, sweep);
     if (c.lx == 0 || c.ly == 0 || c.lz == 0) R.dmask[c.cell] = cross;
 }
 
-// Global site index of the tile-local root stored for global site g.
-__device__ __forceinline__ int crossing_root(const Rep &R, int TX, int TY, int TZ, int g)
+// ------------------------------------------------ crossing clusters (HBM) --
+// P64[x] = (stamp << 32) | parent.  An entry whose stamp is not the current
+// sweep's is a root (left over from an earlier sweep), so P64 needs no
+// clearing: linking a root is a compare-and-swap from the value just read.
+// The larger root is always hung under the smaller one, so a cluster's root
+// stays its minimum site index.
+__device__ __forceinline__ int pfind(unsigned long long *P, int x, uint32_t stamp)
+{
+#pragma unroll 1
+    for (int it = 0; it < (1 << 20); ++it) {
+        const unsigned long long v = __ldcg(P + x);
+        if ((uint32_t)(v >> 32) != stamp) return x;
+        const int p = (int)(uint32_t)v;
+        // path halving: point x at its grandparent if that is a current link
+        const unsigned long long gv = __ldcg(P + p);
+        if ((uint32_t)(gv >> 32) == stamp) __stcg(P + x, gv);
+        x = p;
+    }
+    return x;
+}
+
+__device__ __forceinline__ bool punite(unsigned long long *P, int a, int b, uint32_t stamp)
+{
+#pragma unroll 1
+    for (int it = 0; it < 65536; ++it) {
+        a = pfind(P, a, stamp);
+        b = pfind(P, b, stamp);
+        if (a == b) return true;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const unsigned long long old = __ldcg(P + b);
+        if ((uint32_t)(old >> 32) == stamp) continue;  // b was linked meanwhile
+        const unsigned long long nv = ((unsigned long long)stamp << 32) | (uint32_t)a;
+        if (atomicCAS(P + b, old, nv) == old) return true;
+    }
+    return false;
+}
+
+// Root of x after all unions of the sweep (plain cached loads).
+__device__ __forceinline__ int proot(const unsigned long long *P, int x, uint32_t stamp)
+{
+#pragma unroll 1
+    for (int it = 0; it < (1 << 20); ++it) {
+        const unsigned long long v = P[x];
+        if ((uint32_t)(v >> 32) != stamp) return x;
+        x = (int)(uint32_t)v;
+    }
+    return x;
+}
+
+// Global site index of the tile-local root stored for the site (cell (x, y,
+// z), offset s) with power-of-two tile edges.
+__device__ __forceinline__ int crossing_root(const Rep &R, const Batch &B, int x, int y, int z, int s)
 {
     const int L = R.L;
-    const int lr = R.L16[g] & 0x7FFF;
-    const int cg = g >> 4;
-    const int x = cg % L, y = (cg / L) % L, z = cg / (L * L);
+    const int lr = R.L16[16 * ((int64_t)x + (int64_t)L * ((int64_t)y + (int64_t)L * z)) + s] & 0x7FFF;
     const int lc = lr >> 4;
-    const int rx = (x / TX) * TX + lc % TX;
-    const int ry = (y / TY) * TY + (lc / TX) % TY;
-    const int rz = (z / TZ) * TZ + lc / (TX * TY);
+    const int rx = (x & ~(B.TX - 1)) + (lc & (B.TX - 1));
+    const int ry = (y & ~(B.TY - 1)) + ((lc >> B.lTX) & (B.TY - 1));
+    const int rz = (z & ~(B.TZ - 1)) + (lc >> (B.lTX + B.lTY));
     return 16 * (rx + L * (ry + L * rz)) + (lr & 15);
 }
 
-// Phase 1 (init) and 2 (unite) over the union pairs that leave a tile:
-// init marks both endpoints' tile-local roots as crossing (bit 15 of their
-// L16 entry) and makes each its own parent in P; unite merges them.
-template <bool UNITE>
-__global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ Batch B)
+// Shared-memory bytes of the resolve stage: the global root of each
+// crossing tile-local root (16 nt ints, slot layout), the tile's L16 entries
+// (slot layout) and flip words.
+__host__ __device__ constexpr size_t resolve_smem_bytes(int nt)
 {
-    const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
-    const Rep &R = B.reps[r];
-    const int TX = B.TX, TY = B.TY, TZ = B.TZ, L = R.L;
-    const int t = threadIdx.x;
-    const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
-    if (!(lx == 0 || ly == 0 || lz == 0)) return;
-    const int64_t tile = blockIdx.x - B.tile_begin[r];
-    const int x = (int)(tile % R.ntx) * TX + lx;
-    const int y = (int)((tile / R.ntx) % R.nty) * TY + ly;
-    const int z = (int)(tile / ((int64_t)R.ntx * R.nty)) * TZ + lz;
-    const int64_t cell = (int64_t)x + (int64_t)L * ((int64_t)y + (int64_t)L * z);
-    uint32_t todo = R.dmask[cell];
-    bool ok = true;
-    while (todo) {
-        const int bit = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int f = bit / 6, k = bit % 6;
-        const int ga = down_vertex_global(x, y, z, L, f, pair_a(k));
-        const int gb = down_vertex_global(x, y, z, L, f, pair_b(k));
-        const int ra = crossing_root(R, TX, TY, TZ, ga);
-        const int rb = crossing_root(R, TX, TY, TZ, gb);
-        if (!UNITE) {
-            R.P[ra] = ra;
-            R.P[rb] = rb;
-            unsigned *w = reinterpret_cast<unsigned *>(R.L16);
-            atomicOr(w + (ra >> 1), 1u << (15 + 16 * (ra & 1)));
-            atomicOr(w + (rb >> 1), 1u << (15 + 16 * (rb & 1)));
-        } else {
-            ok &= gunite(R.P, ra, rb);
-        }
-    }
-    if (!ok) atomicOr(&R.st->status, ST_NOCONVERGE);
+    return (size_t)16 * nt * 4 + (size_t)16 * nt * 2 + (size_t)nt * 2 + 16;
 }
-
-// Shared-memory bytes of the resolve stage: the tile's L16 entries (slot
-// layout) and flip words.
-__host__ __device__ constexpr size_t resolve_smem_bytes(int nt) { return (size_t)16 * nt * 2 + (size_t)nt * 2 + 16; }
 
 // Resolve every site of the calling thread's cell to the global index of
 // its cluster's root and the root's flip bit.  Stages the tile's L16 and F
 // words in shared memory; roots of clusters that stay inside the tile are
-// final, the others are looked up in P.  Called by every thread of the block.
-__device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, uint16_t *ls, uint16_t *fs, int root[16],
+// final; each crossing tile-local root is looked up in P once, by the
+// thread that owns it.  stamp: the links' sweep stamp.  Called by every
+// thread of the block.
+__device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, int *smem, uint32_t stamp, int root[16],
                                              uint32_t &flip)
 {
     const int nt = c.nt;
-    // stage: thread t loads cell t's 16 entries (32 contiguous bytes)
+    int *groot = smem;
+    uint16_t *ls = reinterpret_cast<uint16_t *>(smem + 16 * nt);
+    uint16_t *fs = ls + 16 * nt;
     const uint4 *src = reinterpret_cast<const uint4 *>(R.L16 + 16 * c.cell);
     const uint4 a0 = src[0], a1 = src[1];
     const uint32_t w[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    // global index of each site's tile-local root
+    int g[16];
 #pragma unroll
-    for (int s = 0; s < 16; ++s) ls[lslot(16 * c.t + s, nt)] = (uint16_t)(w[s >> 1] >> (16 * (s & 1)));
+    for (int s = 0; s < 16; ++s) {
+        const uint32_t e = (w[s >> 1] >> (16 * (s & 1))) & 0xFFFFu;
+        ls[lslot(16 * c.t + s, nt)] = (uint16_t)e;
+        const int lr = (int)(e & 0x7FFFu);
+        const int lc = lr >> 4;
+        const int rx = c.ox + (lc & (c.TX - 1));
+        const int ry = c.oy + ((lc >> c.lTX) & (c.TY - 1));
+        const int rz = c.oz + (lc >> (c.lTX + c.lTY));
+        g[s] = 16 * (rx + c.L * (ry + c.L * rz)) + (lr & 15);
+        // a crossing root (its own entry is flagged) is resolved here
+        if ((e & 0x8000u) && lr == 16 * c.t + s) groot[lslot(lr, nt)] = proot(R.P, g[s], stamp);
+    }
     fs[c.t] = R.F[c.cell];
     __syncthreads();
     flip = 0;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
         const int lr = (int)((w[s >> 1] >> (16 * (s & 1))) & 0x7FFFu);
-        const int lc = lr >> 4;
-        const int rx = c.ox + lc % c.TX, ry = c.oy + (lc / c.TX) % c.TY, rz = c.oz + lc / (c.TX * c.TY);
-        int g = 16 * (rx + c.L * (ry + c.L * rz)) + (lr & 15);
         uint32_t fb;
+        int r = g[s];
         if (ls[lslot(lr, nt)] & 0x8000u) {
-            g = root_of(R.P, g);
-            fb = (R.F[g >> 4] >> (g & 15)) & 1u;
+            r = groot[lslot(lr, nt)];
+            fb = (R.F[r >> 4] >> (r & 15)) & 1u;
         } else {
-            fb = (fs[lc] >> (lr & 15)) & 1u;
+            fb = (fs[lr >> 4] >> (lr & 15)) & 1u;
         }
-        root[s] = g;
+        root[s] = r;
         flip |= fb << s;
     }
 }

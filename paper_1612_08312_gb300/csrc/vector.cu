@@ -118,75 +118,68 @@ __global__ void __launch_bounds__(512) vec_local_kernel(const __grid_constant__ 
     const int rep = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[rep];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[rep]);
-    const int nt = c.nt, L = c.L;
-    const int64_t N = R.N;
-    int *lab = smem;
-    uint32_t *plist = reinterpret_cast<uint32_t *>(smem + 16 * nt);
-    int *pcount = smem + 28 * nt;
-    T *proj = reinterpret_cast<T *>(smem + 28 * nt + 4);
-    const int HX = c.TX + 1, HY = c.TY + 1, HZ = c.TZ + 1;
+    const CoreSmem sm = core_smem(smem, c.nt);
+    T *proj = reinterpret_cast<T *>(sm.stage);
     const T *spins = static_cast<const T *>(R.spins);
+    const int64_t N = R.N;
     const uint32_t sweep = (uint32_t)R.st->sweep;
     const uint64_t seed = R.seed;
+    core_prologue(sm);
 
     double rd[3];
     unit_vector_dev<NC>(seed, sweep, TAG_AXIS, 0, rd);
     const T r[3] = {(T)rd[0], (T)rd[1], (T)rd[2]};
 
     // projections s_i . r of the tile's sites and the backward halo
-    for (int idx = threadIdx.x; idx < 16 * HX * HY * HZ; idx += blockDim.x) {
-        const int h = idx >> 4, s = idx & 15;
-        const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-        int gx = c.ox + hx - 1, gy = c.oy + hy - 1, gz = c.oz + hz - 1;
-        gx += (gx < 0) ? L : 0;
-        gy += (gy < 0) ? L : 0;
-        gz += (gz < 0) ? L : 0;
-        const int64_t i = 16 * ((int64_t)gx + (int64_t)L * ((int64_t)gy + (int64_t)L * gz)) + s;
+    const int nh = halo_cells(c.TX, c.TY, c.TZ);
+    for (int idx = threadIdx.x; idx < 16 * nh; idx += blockDim.x) {
+        const int64_t i = 16 * halo_cell(idx >> 4, c.TX, c.TY, c.ox, c.oy, c.oz, c.L) + (idx & 15);
         proj[idx] = project<NC, T>(spins, N, i, r);
     }
     __syncthreads();
 
-    // halo cell of the vertex at backward-shift mask m
-    auto hidx = [&](int m) {
-        return (c.lx + 1 - (m & 1)) + HX * ((c.ly + 1 - ((m >> 1) & 1)) + HY * (c.lz + 1 - ((m >> 2) & 1)));
-    };
     const T K2 = (T)R.K2;
-    uint64_t act = 0;
+    uint32_t act[3] = {0, 0, 0};
     if (R.K2 > 0.0) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            T xq[8];
+        for (int g = 0; g < 3; ++g) {
+            T xb[16];
             uint32_t pos = 0;
 #pragma unroll
-            for (int h = 0; h < 8; ++h) {
-                const int cb = 8 * q + h, f = cb / 12, k = cb % 12;
-                const bool up = k < 6;
-                const int kk = up ? k : k - 6;
-                const int va = pair_a(kk), vb = pair_b(kk);
-                const T pa = up ? proj[16 * hidx(0) + 4 * f + va] : proj[16 * hidx(down_mask(f, va)) + down_bit(f, va)];
-                const T pb = up ? proj[16 * hidx(0) + 4 * f + vb] : proj[16 * hidx(down_mask(f, vb)) + down_bit(f, vb)];
-                xq[h] = A::mul(pa, pb);
-                pos |= (xq[h] > (T)0 ? 1u : 0u) << h;
-            }
-            if (!pos) continue;
-            const uint64_t j = 6 * (uint64_t)c.cell + q;
-            const uint4 wd = philox_call(seed, sweep, TAG_BOND, j);
-            const uint32_t ww[4] = {wd.x, wd.y, wd.z, wd.w};
+            for (int f = 0; f < 4; ++f)
 #pragma unroll
-            for (int h = 0; h < 8; ++h) {
-                if (!((pos >> h) & 1u)) continue;
-                const HalfCompare hc(prob_threshold(A::bond_p(K2, xq[h])));
-                const uint32_t hi = (ww[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
-                bool a = hc.all || hi < hc.thi;
-                if (!hc.all && hi == hc.thi) {
-                    const uint4 wt = philox_call(seed, sweep, TAG_TIE, j);
-                    a = ((word_of(wt, h >> 1) >> (16 * (h & 1))) & 0xFFFFu) < hc.tlo;
+                for (int q = 0; q < 4; ++q) {
+                    const int va = slot_a(g, q), vb = slot_b(g, q);
+                    T pa, pb;
+                    if (slot_up(g, q)) {
+                        pa = proj[16 * halo_index(c, 0) + 4 * f + va];
+                        pb = proj[16 * halo_index(c, 0) + 4 * f + vb];
+                    } else {
+                        pa = proj[16 * halo_index(c, down_mask(f, va)) + down_bit(f, va)];
+                        pb = proj[16 * halo_index(c, down_mask(f, vb)) + down_bit(f, vb)];
+                    }
+                    xb[4 * f + q] = A::mul(pa, pb);
+                    pos |= (xb[4 * f + q] > (T)0 ? 1u : 0u) << (4 * f + q);
                 }
-                act |= (uint64_t)(a ? 1u : 0u) << (8 * q + h);
-            }
+            if (!pos) continue;
+            const uint4 wd = philox_call(seed, sweep, TAG_BOND, 3 * (uint64_t)c.cell + g);
+            const uint32_t ww[4] = {wd.x, wd.y, wd.z, wd.w};
+            uint32_t a = 0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (!((pos >> (4 * f + q)) & 1u)) continue;
+                    const ByteCompare bc(prob_threshold(A::bond_p(K2, xb[4 * f + q])));
+                    const uint32_t byte = (ww[f] >> (8 * q)) & 0xFFu;
+                    bool on = bc.all || byte < bc.t8;
+                    if (!bc.all && !bc.none && byte == bc.t8) on = tie_bits(seed, sweep, c.cell, g, f, q) < bc.t24;
+                    a |= (on && !bc.none ? 1u : 0u) << (4 * f + q);
+                }
+            act[g] = a;
         }
     }
-    local_core(c, R, act, sweep, lab, plist, pcount);
+    local_core(c, R, sm, act[0], act[1], act[2], sweep);
 }
 
 template <int NC, typename T>
@@ -197,11 +190,9 @@ __global__ void __launch_bounds__(512) vec_flip_kernel(const __grid_constant__ B
     const int rep = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[rep];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[rep]);
-    uint16_t *ls = reinterpret_cast<uint16_t *>(smem);
-    uint16_t *fs = ls + 16 * c.nt;
     int root[16];
     uint32_t flip;
-    resolve_cell(c, R, ls, fs, root, flip);
+    resolve_cell(c, R, smem, (uint32_t)R.st->epoch, root, flip);
     if (!flip) return;
     double rd[3];
     unit_vector_dev<NC>(R.seed, (uint32_t)R.st->sweep, TAG_AXIS, 0, rd);
@@ -228,55 +219,53 @@ __global__ void __launch_bounds__(512) vec_flip_kernel(const __grid_constant__ B
 
 // Energy (Eq. 1) and magnetisation of the current configuration: every
 // cell sums the 48 bonds it owns and its 16 spins in FP64; one partial
-// (E, M_x, M_y, M_z) per block.
+// (E, M_x, M_y, M_z) per tile, summed in a fixed order.
 template <int NC, typename T>
-__global__ void __launch_bounds__(CELL_BLOCK) vec_measure_kernel(const __grid_constant__ Batch B)
+__global__ void __launch_bounds__(512) vec_measure_kernel(const __grid_constant__ Batch B)
 {
-    const int rep = find_rep(B.block_begin, B.R, blockIdx.x);
+    extern __shared__ __align__(16) int smem[];
+    double *scratch = reinterpret_cast<double *>(smem);
+    const int rep = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[rep];
-    const int64_t cell = (blockIdx.x - B.block_begin[rep]) * CELL_BLOCK + threadIdx.x;
+    const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[rep]);
+    const int L = R.L;
+    const int64_t N = R.N;
+    const T *sp = static_cast<const T *>(R.spins);
+    const int x = c.ox + c.lx, y = c.oy + c.ly, z = c.oz + c.lz;
+    int64_t cb[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int cx = (m & 1) ? wrap_back(x, L) : x;
+        const int cy = (m & 2) ? wrap_back(y, L) : y;
+        const int cz = (m & 4) ? wrap_back(z, L) : z;
+        cb[m] = 16 * ((int64_t)cx + (int64_t)L * ((int64_t)cy + (int64_t)L * cz));
+    }
     double e = 0.0, M[3] = {0.0, 0.0, 0.0};
-    if (cell < R.ncells) {
-        const int L = R.L;
-        const int64_t N = R.N;
-        const T *sp = static_cast<const T *>(R.spins);
-        const int x = (int)(cell % L), y = (int)((cell / L) % L), z = (int)(cell / ((int64_t)L * L));
-        int64_t cb[8];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int cx = (m & 1) ? (x == 0 ? L - 1 : x - 1) : x;
-            const int cy = (m & 2) ? (y == 0 ? L - 1 : y - 1) : y;
-            const int cz = (m & 4) ? (z == 0 ? L - 1 : z - 1) : z;
-            cb[m] = 16 * ((int64_t)cx + (int64_t)L * ((int64_t)cy + (int64_t)L * cz));
-        }
+    for (int s = 0; s < 16; ++s)
 #pragma unroll
-        for (int s = 0; s < 16; ++s)
+        for (int k = 0; k < NC; ++k) M[k] += (double)sp[k * N + cb[0] + s];
 #pragma unroll
-            for (int k = 0; k < NC; ++k) M[k] += (double)sp[k * N + 16 * cell + s];
+    for (int f = 0; f < 4; ++f) {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
+        for (int k = 0; k < 6; ++k) {
+            const int va = pair_a(k), vb = pair_b(k);
+            const int64_t iu = cb[0] + 4 * f + va, ju = cb[0] + 4 * f + vb;
+            T du = sp[iu] * sp[ju];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const int va = pair_a(k), vb = pair_b(k);
-                // up tetrahedron
-                const int64_t iu = 16 * cell + 4 * f + va, ju = 16 * cell + 4 * f + vb;
-                T du = sp[iu] * sp[ju];
+            for (int q = 1; q < NC; ++q) du += sp[q * N + iu] * sp[q * N + ju];
+            const int64_t id = cb[down_mask(f, va)] + down_bit(f, va);
+            const int64_t jd = cb[down_mask(f, vb)] + down_bit(f, vb);
+            T dd = sp[id] * sp[jd];
 #pragma unroll
-                for (int c = 1; c < NC; ++c) du += sp[c * N + iu] * sp[c * N + ju];
-                // down tetrahedron
-                const int64_t id = cb[down_mask(f, va)] + down_bit(f, va);
-                const int64_t jd = cb[down_mask(f, vb)] + down_bit(f, vb);
-                T dd = sp[id] * sp[jd];
-#pragma unroll
-                for (int c = 1; c < NC; ++c) dd += sp[c * N + id] * sp[c * N + jd];
-                e += (double)du + (double)dd;
-            }
+            for (int q = 1; q < NC; ++q) dd += sp[q * N + id] * sp[q * N + jd];
+            e += (double)du + (double)dd;
         }
     }
-    const double se = block_sum_f64(e);
-    const double s0 = block_sum_f64(M[0]);
-    const double s1 = block_sum_f64(M[1]);
-    const double s2 = block_sum_f64(M[2]);
+    const double se = tile_sum_f64(e, c.nt, scratch);
+    const double s0 = tile_sum_f64(M[0], c.nt, scratch);
+    const double s1 = tile_sum_f64(M[1], c.nt, scratch);
+    const double s2 = tile_sum_f64(M[2], c.nt, scratch);
     if (threadIdx.x == 0) {
         double *o = B.partials + 4 * (int64_t)blockIdx.x;
         o[0] = se;
@@ -307,14 +296,15 @@ __global__ void __launch_bounds__(CELL_BLOCK) vec_init_kernel(const __grid_const
 
 // ------------------------------------------------------------ launchers --
 size_t resolve_smem(const TileShape &t);
-void launch_boundary(int unite, const Batch &B, int64_t ntiles, cudaStream_t s);
+void launch_boundary(const Batch &B, int64_t ntiles, cudaStream_t s);
 
 size_t vec_local_smem(const TileShape &t, int prec)
 {
-    const int nt = t.TX * t.TY * t.TZ;
-    return core_smem_bytes(nt) +
-           (prec == PYRO_FP64 ? vec_halo_bytes<double>(t.TX, t.TY, t.TZ) : vec_halo_bytes<float>(t.TX, t.TY, t.TZ));
+    const size_t es = prec == PYRO_FP64 ? 8 : 4;
+    return core_smem_bytes(t.TX * t.TY * t.TZ) + (size_t)16 * halo_cells(t.TX, t.TY, t.TZ) * es;
 }
+
+static size_t vec_measure_smem(const TileShape &t) { return (size_t)t.TX * t.TY * t.TZ * sizeof(double); }
 
 template <int NC, typename T>
 struct VecOps {
@@ -336,12 +326,13 @@ struct VecOps {
         const TileShape t{B.TX, B.TY, B.TZ};
         const int nt = B.TX * B.TY * B.TZ;
         if (p == 0) vec_local_kernel<NC, T><<<(unsigned)ntiles, nt, vec_local_smem(t, prec), s>>>(B);
-        else if (p == 1 || p == 2) launch_boundary(p == 2, B, ntiles, s);
+        else if (p == 1) launch_boundary(B, ntiles, s);
         else vec_flip_kernel<NC, T><<<(unsigned)ntiles, nt, resolve_smem(t), s>>>(B);
     }
-    static void measure(const Batch &B, int64_t nblocks, cudaStream_t s)
+    static void measure(const Batch &B, int64_t ntiles, cudaStream_t s)
     {
-        vec_measure_kernel<NC, T><<<(unsigned)nblocks, CELL_BLOCK, 0, s>>>(B);
+        const TileShape t{B.TX, B.TY, B.TZ};
+        vec_measure_kernel<NC, T><<<(unsigned)ntiles, B.TX * B.TY * B.TZ, vec_measure_smem(t), s>>>(B);
     }
 };
 
@@ -365,17 +356,15 @@ void vec_launch_init(int model, int prec, const Batch &B, int64_t nblocks, int r
     PYRO_VEC_DISPATCH(model, prec, init(B, nblocks, random, s));
 }
 
-// Phase p of a sweep: 0 local labelling, 1 boundary init, 2 boundary unite,
-// 3 flip.
-void vec_launch_phase(int p, int model, int prec, const Batch &B, int64_t ntiles, int64_t nblocks, cudaStream_t s)
+// Phase p of a sweep: 0 local labelling, 1 crossing unions, 2 flip.
+void vec_launch_phase(int p, int model, int prec, const Batch &B, int64_t ntiles, cudaStream_t s)
 {
     PYRO_VEC_DISPATCH(model, prec, phase(p, B, ntiles, prec, s));
-    (void)nblocks;
 }
 
-void vec_launch_measure(int model, int prec, const Batch &B, int64_t nblocks, cudaStream_t s)
+void vec_launch_measure(int model, int prec, const Batch &B, int64_t ntiles, cudaStream_t s)
 {
-    PYRO_VEC_DISPATCH(model, prec, measure(B, nblocks, s));
+    PYRO_VEC_DISPATCH(model, prec, measure(B, ntiles, s));
 }
 
 }  // namespace pyro

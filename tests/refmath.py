@@ -182,14 +182,21 @@ def _stream_calls(seed: int, sweep_field: int, tag: int, j: np.ndarray) -> np.nd
     return curand_philox(ctr, key)
 
 
-def stream_halves(seed: int, sweep_field: int, tag: int, idx: np.ndarray) -> np.ndarray:
-    """16-bit half x of a (seed, sweep, tag) stream via cuRAND: half x & 7
-    (bits 16 (h & 1) and up of output word h >> 1) of call x >> 3."""
+def stream_bytes(seed: int, sweep_field: int, tag: int, idx: np.ndarray) -> np.ndarray:
+    """Byte x of a (seed, sweep, tag) stream via cuRAND: byte x & 15 (bits
+    8 (x & 3) and up of output word (x & 15) >> 2) of call x >> 4."""
     idx = np.asarray(idx, dtype=np.uint64)
-    out = _stream_calls(seed, sweep_field, tag, idx >> np.uint64(3))
-    h = (idx & np.uint64(7)).astype(np.int64)
-    w = out[np.arange(len(idx)), h >> 1]
-    return ((w >> (16 * (h & 1)).astype(np.uint32)) & np.uint32(0xFFFF)).astype(np.uint32)
+    out = _stream_calls(seed, sweep_field, tag, idx >> np.uint64(4))
+    t = (idx & np.uint64(15)).astype(np.int64)
+    w = out[np.arange(len(idx)), t >> 2]
+    return ((w >> (8 * (t & 3)).astype(np.uint32)) & np.uint32(0xFF)).astype(np.uint32)
+
+
+def stream_words(seed: int, sweep_field: int, tag: int, idx: np.ndarray) -> np.ndarray:
+    """Word x of a stream via cuRAND: output word x & 3 of call x >> 2."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    out = _stream_calls(seed, sweep_field, tag, idx >> np.uint64(2))
+    return out[np.arange(len(idx)), (idx & np.uint64(3)).astype(np.int64)]
 
 
 def stream_bits(seed: int, sweep_field: int, tag: int, idx: np.ndarray) -> np.ndarray:
@@ -202,9 +209,22 @@ def stream_bits(seed: int, sweep_field: int, tag: int, idx: np.ndarray) -> np.nd
     return ((w >> (t & 31).astype(np.uint32)) & np.uint32(1)).astype(np.uint32)
 
 
-def bond_words(seed: int, sweep: int, bonds: np.ndarray) -> np.ndarray:
-    """32-bit uniform of each bond: BOND-stream half as the high 16 bits,
-    TIE-stream half (tag 5) as the low 16 bits."""
-    hi = stream_halves(seed, sweep, 1, bonds).astype(np.uint64)
-    lo = stream_halves(seed, sweep, 5, bonds).astype(np.uint64)
-    return (hi << np.uint64(16)) | lo
+# Random-number id of bond 12 r + k: 48 c + 16 g + 4 f + q (r = 4 c + f), with
+# (g, q) per pair k: up (0,1) (0,2) (0,3) (1,2) (1,3) (2,3), then down likewise.
+RNG_G = np.array([0, 1, 0, 0, 1, 0, 2, 1, 2, 2, 1, 2])
+RNG_Q = np.array([0, 0, 3, 1, 1, 2, 0, 2, 3, 1, 3, 2])
+
+
+def bond_rng_ids(nbonds: int) -> np.ndarray:
+    b = np.arange(nbonds, dtype=np.int64)
+    r, k = b // 12, b % 12
+    return (48 * (r >> 2) + 16 * RNG_G[k] + 4 * (r & 3) + RNG_Q[k]).astype(np.uint64)
+
+
+def bond_words(seed: int, sweep: int, nbonds: int) -> np.ndarray:
+    """32-bit uniform of each bond 12 r + k: its id's BOND-stream byte as the
+    top 8 bits, the low 24 bits of its TIE-stream word (tag 5) below."""
+    ids = bond_rng_ids(nbonds)
+    hi = stream_bytes(seed, sweep, 1, ids).astype(np.uint64)
+    lo = stream_words(seed, sweep, 5, ids).astype(np.uint64) & np.uint64(0xFFFFFF)
+    return (hi << np.uint64(24)) | lo

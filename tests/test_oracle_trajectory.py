@@ -3,8 +3,8 @@
 A sweep is recomputed step by step in numpy from the spins before it, with
 random numbers from cuRAND's Philox (not the oracle's), clusters from
 scipy.sparse.csgraph, and the bond list from the geometry test's pinned
-tetrahedra.  This pins the index conventions (bond id, call index, 16-bit
-half and single-bit slots, tags, sweep field), the bond rule of each model,
+tetrahedra.  This pins the index conventions (bond random-number id, call
+index, byte / word / bit slots, tags, sweep field), the bond rule of each model,
 the canonical root, the flip and the reflection s -> s - 2 (s.r) r (Wolff
 embedding, Sec. 2)."""
 import math
@@ -62,7 +62,7 @@ def test_ising_sweep_recomputed(L, T, seed):
         s0 = o.spins().astype(np.int64)
         o.sweep(beta, 1)
         sat = s0[bi] == s0[bj]
-        w = refmath.bond_words(seed, k, np.arange(3 * N))
+        w = refmath.bond_words(seed, k, 3 * N)
         thr = math.floor(-math.expm1(-2 * beta) * 2 ** 32)
         act = sat & (w.astype(np.int64) < thr)
         assert (o.active().astype(bool) == act).all()
@@ -100,7 +100,7 @@ def test_vector_sweep_recomputed(model, L, T):
         assert (o.axis() == r).all()
         proj = s0 @ r
         x = proj[bi] * proj[bj]
-        w = refmath.bond_words(seed, k, np.arange(3 * N)).astype(np.float64)
+        w = refmath.bond_words(seed, k, 3 * N).astype(np.float64)
         p = -np.expm1(-2 * beta * np.maximum(x, 0))
         thr = np.floor(p * 2 ** 32)
         act = (x > 0) & (w < thr)
@@ -120,6 +120,14 @@ def test_vector_sweep_recomputed(model, L, T):
         # the reflection reverses the projection on r and keeps |s| = 1
         assert np.allclose(o.spins()[flip] @ r, -proj[flip], atol=1e-14)
         assert np.allclose(np.linalg.norm(o.spins(), axis=1), 1, atol=1e-14)
+
+
+def test_bond_rng_ids_are_a_permutation():
+    # every cell's 48 bonds use 48 distinct ids 48 c .. 48 c + 47
+    o = oracle.Oracle(2, oracle.ISING, 1)
+    ids = np.array([oracle.bond_rng_id(b) for b in range(3 * o.N)])
+    assert (np.sort(ids) == np.arange(3 * o.N)).all()
+    assert (ids == refmath.bond_rng_ids(3 * o.N)).all()
 
 
 def test_clusters_match_scipy_on_random_graphs():
