@@ -62,6 +62,8 @@ def lib():
             L.orc_philox.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p]
             L.orc_bond_word.restype = c.c_uint32
             L.orc_bond_word.argtypes = [c.c_uint64, c.c_uint32, c.c_uint64]
+            L.orc_bond_rng_id.restype = c.c_uint64
+            L.orc_bond_rng_id.argtypes = [c.c_uint64]
             L.orc_threshold.restype = c.c_uint64
             L.orc_threshold.argtypes = [c.c_double, c.c_double]
             L.orc_unit_vector.restype = c.c_int
@@ -91,8 +93,13 @@ def philox(counter, key) -> np.ndarray:
 
 
 def bond_word(seed: int, sweep: int, b: int) -> int:
-    """The 32-bit uniform of bond b in sweep `sweep`."""
+    """The 32-bit uniform of the bond with random-number id b in a sweep."""
     return int(lib().orc_bond_word(seed, sweep, b))
+
+
+def bond_rng_id(bond: int) -> int:
+    """Random-number id of bond 12 r + k."""
+    return int(lib().orc_bond_rng_id(bond))
 
 
 def threshold(beta: float, J: float = 1.0) -> int:

@@ -18,15 +18,21 @@
  * Conventions that the paper leaves open (all listed in the design doc):
  *   - site index i = 16*(x + L*(y + L*z)) + 4*f + mu, position (quarter
  *     units) 4*(x,y,z) + A_f + B_mu;
- *   - bond id b = 12*r + k, r = i >> 2 the FCC point, k = 0..5 the pairs of
- *     the "up" tetrahedron of r, k = 6..11 the pairs of the "down"
+ *   - bonds grouped by tetrahedron: bond 12*r + k, r = i >> 2 the FCC point,
+ *     k = 0..5 the vertex pairs (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) of the
+ *     "up" tetrahedron of r, k = 6..11 the same pairs of the "down"
  *     tetrahedron whose basis-0 vertex is site 4r;
+ *   - the random-number id of a bond of cell c, FCC sub-point f:
+ *     b = 48 c + 16 g + 4 f + q with (g, q) = (0,0) up (0,1), (0,1) up (1,2),
+ *     (0,2) up (2,3), (0,3) up (0,3), (1,0) up (0,2), (1,1) up (1,3),
+ *     (1,2) down (0,2), (1,3) down (1,3), (2,0) down (0,1), (2,1) down
+ *     (1,2), (2,2) down (2,3), (2,3) down (0,3);
  *   - random numbers from Philox4x32-10 keyed by the seed, counter
- *     (j_lo, j_hi, sweep, tag).  A call yields 128 bits, read as eight
- *     16-bit halves (half h = bits 16 (h & 1) .. of output word h >> 1) or
- *     as 128 single bits (bit t = bit t & 31 of output word t >> 5);
- *   - bond b's 32-bit uniform w_b: high half = half (b & 7) of BOND call
- *     b >> 3, low half = half (b & 7) of TIE call b >> 3;
+ *     (j_lo, j_hi, sweep, tag).  A call yields 128 bits, read as sixteen
+ *     bytes (byte t = bits 8 (t & 3) .. of output word t >> 2), four words,
+ *     or 128 single bits (bit t = bit t & 31 of output word t >> 5);
+ *   - bond b's 32-bit uniform w_b: top 8 bits = byte (b & 15) of BOND call
+ *     b >> 4, low 24 bits = low 24 bits of word (b & 3) of TIE call b >> 2;
  *   - one flip bit per cluster: bit (root & 127) of FLIP call root >> 7;
  *   - canonical cluster label = minimum site index of the cluster.
  *
@@ -87,13 +93,21 @@ static void stream_call(uint64_t seed, uint32_t sweep_field, uint32_t tag, uint6
     orc_philox(ctr, key, out);
 }
 
-/* Half x of the stream (seed, sweep field, tag): 16-bit half x & 7 of the
- * Philox call with call index x >> 3. */
-static uint32_t stream_half(uint64_t seed, uint32_t sweep_field, uint32_t tag, uint64_t x)
+/* Byte x of the stream (seed, sweep field, tag): byte x & 15 of the Philox
+ * call with call index x >> 4. */
+static uint32_t stream_byte(uint64_t seed, uint32_t sweep_field, uint32_t tag, uint64_t x)
 {
     uint32_t out[4];
-    stream_call(seed, sweep_field, tag, x >> 3, out);
-    return (out[(x & 7) >> 1] >> (16 * (x & 1))) & 0xFFFFu;
+    stream_call(seed, sweep_field, tag, x >> 4, out);
+    return (out[(x & 15) >> 2] >> (8 * (x & 3))) & 0xFFu;
+}
+
+/* Word x of the stream: output word x & 3 of the call with index x >> 2. */
+static uint32_t stream_word(uint64_t seed, uint32_t sweep_field, uint32_t tag, uint64_t x)
+{
+    uint32_t out[4];
+    stream_call(seed, sweep_field, tag, x >> 2, out);
+    return out[x & 3];
 }
 
 /* Bit x of the stream: bit x & 127 of the Philox call with index x >> 7. */
@@ -104,10 +118,22 @@ static uint32_t stream_bit(uint64_t seed, uint32_t sweep_field, uint32_t tag, ui
     return (out[(x & 127) >> 5] >> (x & 31)) & 1u;
 }
 
-/* The 32-bit uniform of bond b in a sweep. */
+/* The 32-bit uniform of the bond with random-number id b in a sweep. */
 uint32_t orc_bond_word(uint64_t seed, uint32_t sweep_field, uint64_t b)
 {
-    return (stream_half(seed, sweep_field, TAG_BOND, b) << 16) | stream_half(seed, sweep_field, TAG_TIE, b);
+    return (stream_byte(seed, sweep_field, TAG_BOND, b) << 24) |
+           (stream_word(seed, sweep_field, TAG_TIE, b) & 0xFFFFFFu);
+}
+
+/* Random-number id of bond 12 r + k (see the header comment). */
+static const int RNG_G[12] = {0, 1, 0, 0, 1, 0, 2, 1, 2, 2, 1, 2};
+static const int RNG_Q[12] = {0, 0, 3, 1, 1, 2, 0, 2, 3, 1, 3, 2};
+
+uint64_t orc_bond_rng_id(uint64_t bond)
+{
+    uint64_t r = bond / 12, k = bond % 12;
+    uint64_t c = r >> 2, f = r & 3;
+    return 48 * c + 16 * (uint64_t)RNG_G[k] + 4 * f + (uint64_t)RNG_Q[k];
 }
 
 /* Threshold of a bond with activation probability p: the bond is active iff
@@ -437,7 +463,7 @@ static void sweep_once(orc *h, double beta, double *trace)
             int32_t i = h->bond_i[b], j = h->bond_j[b];
             int act = 0;
             if (h->sigma[i] == h->sigma[j]) {
-                uint32_t w = orc_bond_word(h->seed, sw, (uint64_t)b);
+                uint32_t w = orc_bond_word(h->seed, sw, orc_bond_rng_id((uint64_t)b));
                 act = ((uint64_t)w < thr);
             }
             h->active[b] = (uint8_t)act;
@@ -455,7 +481,7 @@ static void sweep_once(orc *h, double beta, double *trace)
             int act = 0;
             if (x > 0.0) {
                 double prob = -expm1(-(K2 * x));
-                uint32_t w = orc_bond_word(h->seed, sw, (uint64_t)b);
+                uint32_t w = orc_bond_word(h->seed, sw, orc_bond_rng_id((uint64_t)b));
                 act = ((uint64_t)w < prob_threshold(prob));
             }
             h->active[b] = (uint8_t)act;
