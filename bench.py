@@ -2,10 +2,13 @@
 """Benchmark: Swendsen-Wang sweeps of the pyrochlore Ising model on GB300.
 
 One step = one full Swendsen-Wang sweep (bond activation, tile-local and
-global labelling, cluster flips, E / m^2 / m^4 measurement and accumulation)
-of the L = 256 Ising lattice (N = 16 * 256^3 = 268,435,456 sites) at
-T = 4.21394, from a Philox-random start -- the workload the headline metric
-is quoted on.  The metric is site updates per nanosecond (N * steps / time).
+global labelling, cluster flips, E / m^2 / m^4 measurement and accumulation).
+Default workload: the L = 256 Ising lattice (N = 16 * 256^3 = 268,435,456
+sites) at T = 4.21394 from a Philox-random start, the workload the headline
+metric is quoted on.  --workload selects the other runs (L = 8 Ising, 48
+batched Ising replicas, XY L = 64 in FP32 with the plain FP64 form beside it,
+24 batched Heisenberg replicas likewise).  The metric is site updates per
+nanosecond (sites * steps / time).
 
 Multi-GPU: independent replicas, one lattice per rank with its own seed (the
 sweep of one lattice does not shard), so scaling is weak and there is no
@@ -34,17 +37,17 @@ import workloads  # noqa: E402
 METRIC = "SW site-updates/ns on 1 GB300 (% HBM roofline); batched+FP32 vs plain"
 UNIT = "site-updates/ns"
 FALLBACK_HBM_GBS = 6800.0
-# Algorithmic bytes per site of one sweep (bit-packed spins read + written,
-# one int32 label written and read): the whole-sweep HBM model.
-SWEEP_BYTES_PER_SITE = 8.25
-# Bytes per site each phase of the Ising sweep must move in HBM.
-PHASE_BYTES_PER_SITE = {
-    "local": 0.125 + 2.0 + 0.125,   # spin words read; 16-bit local labels and flip words written
-    "boundary": 0.0,                # only tile-crossing pairs; not credited
-    "flip": 2.0 + 0.125 + 0.25,     # local labels and flip words read; spin words read and written
-    "measure": 0.125,               # spin words read
-    "accumulate": 0.0,
-}
+# Algorithmic bytes per site update of one sweep: one int32 label written
+# and read, the spins read and written (Ising bit-packed: 1/8 byte each way;
+# n-vector: n components of 4 or 8 bytes each way).
+SWEEP_BYTES = {1: {0: 8.25, 1: 8.25}, 2: {0: 24.0, 1: 40.0}, 3: {0: 32.0, 1: 56.0}}
+SWEEP_BYTES_PER_SITE = SWEEP_BYTES[1][1]
+# The Ising sweep's 8.25 bytes split over its kernels: the local kernel
+# reads the spins and writes the labels, the flip kernel reads the labels
+# and writes the spins; the crossing unions, measurement and accumulation
+# move nothing the model counts.
+PHASE_BYTES_PER_SITE = {"local": 0.125 + 4.0, "boundary": 0.0, "flip": 4.0 + 0.125, "measure": 0.0,
+                        "accumulate": 0.0}
 KERNEL_NAMES = {"local": "ising_local_kernel", "boundary": "boundary_kernel", "flip": "ising_flip_kernel",
                 "measure": "ising_measure_kernel", "accumulate": "accumulate_kernel"}
 
@@ -70,17 +73,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def committed_traffic(kernel: str, nsites: int):
+    """DRAM bytes per launch of `kernel` on an nsites lattice, from the
+    committed ncu summary (bytes per site of the captured case), if it was
+    taken on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     src = kernel_source_hash()
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[3] == src:
-            return float(parts[1]) * float(parts[2])  # bytes per site * sites of the bench lattice
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel and parts[2] == src:
+            return float(parts[1]) * nsites
     return None
 
 
@@ -136,11 +140,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(L: int, T: float, seconds: float = 12.0, max_sweeps: int = 40):
-    """Time the oracle (single-threaded C) on a bounded sample: an L-lattice
-    Ising run at temperature T from the random start."""
+def cpu_baseline(wl: dict, args, seconds: float = 12.0, max_sweeps: int = 40):
+    """Time the oracle (single-threaded C) on a bounded sample of the
+    workload: one L = 32 lattice of the workload's model and temperature
+    (L = 8 for the L = 8 workload) from the random start."""
     import oracle
-    o = oracle.Oracle(L, oracle.ISING, 1, "random")
+    L = 8 if args.workload == "ising_L8" else 32
+    T = wl["T"]
+    o = oracle.Oracle(L, wl["model"], 1, "random")
     o.sweep(1.0 / T, 1)
     n, t0 = 0, time.perf_counter()
     while n < max_sweeps and time.perf_counter() - t0 < seconds:
@@ -148,8 +155,8 @@ def cpu_baseline(L: int, T: float, seconds: float = 12.0, max_sweeps: int = 40):
         n += 1
     dt = time.perf_counter() - t0
     return {"value": o.N * n / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle, Ising L={L} (N={o.N}) at T={T}, random start, {n} timed sweeps after 1 "
-                      f"untimed ({dt:.1f} s, single thread)"}
+            "sample": f"oracle, model {wl['model']} L={L} (N={o.N}) at T={T}, random start, {n} timed sweeps "
+                      f"after 1 untimed ({dt:.1f} s, single thread)"}
 
 
 def dist_setup():
@@ -159,29 +166,69 @@ def dist_setup():
     return world, rank, local
 
 
+def rank_seed(base: int, rank: int) -> int:
+    """Seed of the independent replica a rank runs (ranks never share a chain)."""
+    return (base + rank * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max over ranks of a per-rank time (the job ends when the slowest rank does)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    cfg = workloads.ISING_L256
-    T = cfg["T"][1]
-    L = args.ref_L
+    wl = WORKLOADS[args.workload]
+    model, T, L = wl["model"], wl["T"], args.ref_L
     import oracle
-    o = oracle.Oracle(L, oracle.ISING, 1, "random")
+    o = oracle.Oracle(L, model, 1, "random")
     for _ in range(args.warmup):
         o.sweep(1.0 / T, 1)
     t0 = time.perf_counter()
     o.sweep(1.0 / T, args.steps)
     dt = time.perf_counter() - t0
     value = o.N * args.steps / (dt * 1e9)
-    sample = (f"oracle, Ising L={L} (N={o.N}) at T={T}, random start; each step one sweep of this "
-              f"bounded sample of the L=256 workload; single thread")
+    sample = (f"oracle, model {model} L={L} (N={o.N}) at T={T}, random start; each step one sweep of this "
+              f"bounded sample of the {args.workload} workload; single thread")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-           "config": {"workload": "ising_L256", "L": 256, "T": T, "sample_L": L},
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype_ref"],
+           "data": "synthetic", "config": {"workload": args.workload, "sample_L": L, "T": T},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+# Workloads (sizes, temperatures and starts of the paper's kind of run;
+# see workloads/__init__.py).  Batched replicas use seed + r * golden.
+WORKLOADS = {
+    "ising_L256": dict(model=1, L=256, T=4.21394, start="random", seed=1, precision=1, dtype="u8", dtype_ref="i8"),
+    "ising_L8": dict(model=1, L=8, T=4.21394, start="up", seed=1, precision=1, dtype="u8", dtype_ref="i8"),
+    "ising_batch48": dict(model=1, Ls=workloads.ISING_BATCH["L"], Ts=workloads.ISING_BATCH["T"], T=4.21394,
+                          start="random", seed=1, precision=1, dtype="u8", dtype_ref="i8"),
+    "xy_L64": dict(model=2, L=64, T=2.0285, start="random", seed=1, precision=0, dtype="f32", dtype_ref="f64"),
+    "heis_batch24": dict(model=3, Ls=workloads.HEIS_BATCH["L"], Ts=workloads.HEIS_BATCH["T"], T=1.31695,
+                         start="random", seed=1, precision=0, dtype="f32", dtype_ref="f64"),
+}
+
+
+def time_device(stream, fn):
+    """Device ms of fn() between two CUDA events on the given stream."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
 
 
 def main():
@@ -190,10 +237,13 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--L", type=int, default=256)
+    ap.add_argument("--workload", default="ising_L256", choices=list(WORKLOADS))
+    ap.add_argument("--L", type=int, default=0, help="override the lattice size of a single-lattice workload")
+    ap.add_argument("--tile", default="auto", help="'auto' (autotuner), 'default', or TXxTYxTZ")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--ref-L", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 arm of n-vector workloads")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -208,99 +258,180 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_1612_08312_gb300 as pyro
 
-    cfg = workloads.ISING_L256
-    T = cfg["T"][1]
-    beta = 1.0 / T
-    L = args.L
-    seed = cfg["seeds"][0] + rank  # one independent replica per rank
-    lat = pyro.Lattice(L, pyro.ISING, seed, start="random")
-    N = lat.N
-    stream = torch.cuda.ExternalStream(pyro.pyro_get_stream(lat.h))
-
-    lat.sweep(beta, max(args.warmup, 3))
-    lat.sync()
+    wl = WORKLOADS[args.workload]
+    model, prec = wl["model"], wl["precision"]
+    peak, peak_kind = peaks()
 
     def barrier():
         if world > 1:
             dist.barrier()
 
+    batched = "Ls" in wl
+    if batched:
+        reps = [(L, T) for L in wl["Ls"] for T in wl["Ts"]]
+        Ls, betas = [r[0] for r in reps], [1.0 / r[1] for r in reps]
+        obj = pyro.Replicas(Ls, betas, model, precision=prec, start=wl["start"], seed=rank_seed(wl["seed"], rank))
+        N = obj.total_sites
+        stream = torch.cuda.ExternalStream(obj.stream)
+        sweep = lambda n: obj.sweep(n)
+        sync = obj.sync
+        tile = None
+    else:
+        L = args.L or wl["L"]
+        beta = 1.0 / wl["T"]
+        if args.tile == "auto":
+            tile = pyro.pyro_autotune(L, model, prec, beta, 3)[0]
+        elif args.tile == "default":
+            tile = (0, 0, 0)
+        else:
+            tile = tuple(int(v) for v in args.tile.split("x"))
+        obj = pyro.Lattice(L, model, rank_seed(wl["seed"], rank), precision=prec, start=wl["start"], tile=tile)
+        N = obj.N
+        stream = torch.cuda.ExternalStream(pyro.pyro_get_stream(obj.h))
+        sweep = lambda n: obj.sweep(beta, n)
+        sync = obj.sync
+        tile = list(obj.tile)
+
+    sweep(max(args.warmup, 3))
+    sync()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    lat.sync()
-    l0 = lat.launches
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    lat.sweep(beta, args.steps)
-    e1.record(stream)
-    e1.synchronize()
-    lat.sync()
+    sync()
+    l0 = obj.launches
+    ms = time_device(stream, lambda: sweep(args.steps))
+    sync()
+    launches = obj.launches - l0
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
-    launches = lat.launches - l0
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, world, device="cuda")
     value = N * args.steps * world / (ms * 1e6)
 
-    # per-phase device times (event-bracketed) for the roofline of the dominant kernel
-    prof = pyro.pyro_profile_phases(lat.h, beta, 5)
-    dominant = max(prof, key=prof.get)
-    peak, peak_kind = peaks()
-    alg_bytes = PHASE_BYTES_PER_SITE[dominant] * N
-    achieved = alg_bytes / (prof[dominant] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dominant], "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": committed_traffic(KERNEL_NAMES[dominant]),
-                "alg_bytes_per_site": PHASE_BYTES_PER_SITE[dominant],
-                "phase_ms": {k: round(v, 5) for k, v in prof.items()}}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+           "config": {"workload": args.workload, "N": N, "model": model, "start": wl["start"],
+                      "tile": tile, "parallelism": f"replicas{world}",
+                      "l2": "inputs larger than L2" if N * 4 > 129e6 else "working set may fit in L2"},
+           "gpu_launches": launches, "clocks": clk}
+    if batched:
+        out["config"].update({"replicas": len(reps), "L": sorted(set(Ls)), "T": wl["Ts"], "graphs": True})
+    else:
+        out["config"].update({"L": L, "T": wl["T"]})
 
-    # end to end through the C ABI with host buffers: per step the state
-    # goes host -> device, one sweep runs, the state and the measurement come
-    # back device -> host
-    nbytes = pyro.pyro_state_bytes(lat.h)
-    host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-    host_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-    pyro.pyro_get_state(lat.h, host_in.data_ptr(), nbytes)
-    lat.sync()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        pyro.pyro_set_state(lat.h, host_in.data_ptr(), nbytes)
-        lat.sweep(beta, 1)
-        pyro.pyro_get_state(lat.h, host_out.data_ptr(), nbytes)
-        lat.measure()  # synchronises; E, m^2, m^4 to the host
-        host_in, host_out = host_out, host_in
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": N * args.e2e_steps * world / (e2e_s * 1e9), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes + 24, "steps": args.e2e_steps}
+    if not batched and model == 1:
+        prof = pyro.pyro_profile_phases(obj.h, beta, 5)
+        dominant = max(prof, key=prof.get)
+        alg_bytes = PHASE_BYTES_PER_SITE[dominant] * N
+        achieved = alg_bytes / (prof[dominant] * 1e-3) / 1e9
+        traffic = committed_traffic(KERNEL_NAMES[dominant], N)
+        out["roofline"] = {"bound": "hbm", "kernel": KERNEL_NAMES[dominant], "achieved": achieved, "peak": peak,
+                           "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                           "alg_bytes_per_site": PHASE_BYTES_PER_SITE[dominant],
+                           "phase_ms": {k: round(v, 5) for k, v in prof.items()}}
+    else:
+        out["roofline"] = {"bound": "hbm", "kernel": "whole sweep", "achieved": value * SWEEP_BYTES[model][prec],
+                           "peak": peak, "unit": "GB/s", "frac": value * SWEEP_BYTES[model][prec] / peak,
+                           "peak_kind": peak_kind, "traffic": None,
+                           "alg_bytes_per_site": SWEEP_BYTES[model][prec]}
+    out["sweep_hbm_frac"] = value * SWEEP_BYTES[model][prec] / peak
 
-    out = None
+    # end to end through the C ABI with host buffers (single lattices): per
+    # step the state goes host -> device, one sweep runs, the state and the
+    # measurement come back device -> host
+    if not batched:
+        nbytes = pyro.pyro_state_bytes(obj.h)
+        host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        host_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        pyro.pyro_get_state(obj.h, host_in.data_ptr(), nbytes)
+        sync()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            pyro.pyro_set_state(obj.h, host_in.data_ptr(), nbytes)
+            sweep(1)
+            pyro.pyro_get_state(obj.h, host_out.data_ptr(), nbytes)
+            obj.measure()  # synchronises; E, m^2, m^4 to the host
+            host_in, host_out = host_out, host_in
+        e2e_s = reduce_max(time.perf_counter() - t0, world, device="cuda")
+        out["e2e"] = {"value": N * args.e2e_steps * world / (e2e_s * 1e9), "unit": UNIT,
+                      "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 24, "steps": args.e2e_steps}
+    else:
+        # a batch's state stays on the device; per step the host reads every
+        # replica's measurement
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            obj.sweep(1)
+            for r in range(len(reps)):
+                obj.measure(r)
+        e2e_s = reduce_max(time.perf_counter() - t0, world, device="cuda")
+        out["e2e"] = {"value": N * args.e2e_steps * world / (e2e_s * 1e9), "unit": UNIT,
+                      "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 24 * len(reps), "steps": args.e2e_steps}
+
+    # n-vector workloads: the plain FP64 form (per-replica launches, no
+    # graph) on the same sweeps, and the Binder ratio from both chains
+    if model != 1 and not args.no_compare and rank == 0:
+        out["vs_plain_fp64"] = compare_plain_fp64(pyro, wl, args, obj, batched, value)
+
     if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-               "config": {"workload": "ising_L256", "L": L, "N": N, "T": T, "start": "random",
-                          "tile": list(lat.tile), "parallelism": f"replicas{world}",
-                          "l2": "inputs larger than L2 (labels 4N bytes)"},
-               "sweep_hbm_frac": value * SWEEP_BYTES_PER_SITE / peak,
-               "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
-        if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(64, T)
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(wl, args)
         print(json.dumps(out))
-    lat.close()
+    obj.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def compare_plain_fp64(pyro, wl, args, obj, batched, value_fast):
+    """Time the plain form: FP64 spins, one lattice per replica, separate
+    launches (no CUDA graph), the same number of sweeps; and the Binder
+    ratio with its jackknife error from per-sweep traces of both forms."""
+    import numpy as np
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    model = wl["model"]
+    reps = [(L, T) for L in wl["Ls"] for T in wl["Ts"]] if batched else [(args.L or wl["L"], wl["T"])]
+    lats = [pyro.Lattice(L, model, 7 + r, precision=pyro.FP64, start=wl["start"]) for r, (L, T) in enumerate(reps)]
+    for lat in lats:
+        lat.set_graphs(False)
+    n = max(args.steps // 4, 10)
+    for lat, (L, T) in zip(lats, reps):
+        lat.sweep(1.0 / T, 2)
+    for lat in lats:
+        lat.sync()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        for lat, (L, T) in zip(lats, reps):
+            lat.sweep(1.0 / T, 1)
+    for lat in lats:
+        lat.sync()
+    dt = time.perf_counter() - t0
+    total = sum(16 * L ** 3 for L, _ in reps)
+    value_plain = total * n / (dt * 1e9)
+    # Binder ratio of the smallest replica from both forms (same sweep count)
+    L0, T0 = reps[0]
+    fast = pyro.Lattice(L0, model, 11, precision=pyro.FP32, start=wl["start"])
+    plain = pyro.Lattice(L0, model, 13, precision=pyro.FP64, start=wl["start"])
+    plain.set_graphs(False)
+    nb = 4000
+    res = {}
+    for name, lat in (("fp32_graph", fast), ("fp64_plain", plain)):
+        lat.sweep(1.0 / T0, 200)
+        pyro.pyro_set_trace(lat.h, nb)
+        lat.sweep(1.0 / T0, nb)
+        tr = pyro.pyro_get_trace(lat.h, nb)
+        from refmath import jackknife_ratio
+        U, err = jackknife_ratio(tr[:, 1], tr[:, 2], 40)
+        res[name] = {"U": U, "U_err": err}
+        lat.close()
+    for lat in lats:
+        lat.close()
+    return {"value": value_plain, "unit": UNIT, "ratio": value_fast / value_plain, "sweeps": n,
+            "form": "FP64 spins, one lattice per replica, one launch per phase (no graph)",
+            "binder": {"L": L0, "T": T0, "sweeps": nb, **res}}
 
 
 if __name__ == "__main__":

@@ -176,6 +176,30 @@ void *pyro_get_stream(pyro_handle h);
 /* Number of kernel launches this handle has issued (for accounting). */
 uint64_t pyro_launch_count(pyro_handle h);
 
+/* Whether multi-sweep calls replay captured CUDA graphs (default on; only
+ * with a library-owned stream).  Off = one launch per phase per sweep. */
+int pyro_set_graphs(pyro_handle h, int on);
+
+/* Autotuner: time every candidate labelling tile (power-of-two edges
+ * dividing L, 64 to 512 cells) on a scratch lattice for nsweeps sweeps at
+ * beta and return the fastest in tile_out (pass it in pyro_config.tile) and
+ * its device ms per sweep (NULL allowed).  Results are cached per (GPU
+ * name, L, model, precision) in the process and, if the environment
+ * variable PYRO_AUTOTUNE_CACHE names a file, across processes.  Allocates
+ * and frees a scratch lattice per candidate; synchronises the device. */
+int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int tile_out[3], double *ms_per_sweep);
+
+/* Test hooks for failure handling, process-wide:
+ *   PYRO_DEBUG_FAIL_ALLOCS  the next `value` device allocations made while
+ *                           creating a lattice or batch report failure
+ *                           (the call returns PYRO_E_NOMEM, nothing leaks);
+ *   PYRO_DEBUG_UNITE_BOUND  iteration bound of one shared-memory union
+ *                           (default 4096; 0 makes every union give up at
+ *                           once, so the next synchronising call returns
+ *                           PYRO_E_NOCONVERGE). */
+enum { PYRO_DEBUG_FAIL_ALLOCS = 1, PYRO_DEBUG_UNITE_BOUND = 2 };
+int pyro_debug_set(int key, int64_t value);
+
 /* Tracing: run n sweeps at beta like pyro_sweep, but as separate launches
  * bracketed by CUDA events, and return the mean device time in ms of each
  * of the five phases of a sweep in phase_ms[0..4]: tile-local labelling
@@ -248,6 +272,7 @@ int pyro_batch_measure(pyro_batch b, int r, double *E, double *m2, double *m4);
 int pyro_batch_get_spins(pyro_batch b, int r, void *host, size_t bytes);
 int pyro_batch_sync(pyro_batch b);
 int64_t pyro_batch_total_sites(pyro_batch b);
+void *pyro_batch_get_stream(pyro_batch b);
 uint64_t pyro_batch_launch_count(pyro_batch b);
 void pyro_batch_destroy(pyro_batch b);
 

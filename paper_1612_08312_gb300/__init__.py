@@ -73,6 +73,10 @@ _SIGS = {
     "pyro_launch_count": (ctypes.c_uint64, [ctypes.c_void_p]),
     "pyro_profile_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_double)]),
+    "pyro_set_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "pyro_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "pyro_debug_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64]),
     "pyro_destroy": (None, [ctypes.c_void_p]),
     "pyro_last_error": (ctypes.c_char_p, []),
     "pyro_batch_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
@@ -86,6 +90,7 @@ _SIGS = {
     "pyro_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "pyro_batch_total_sites": (ctypes.c_int64, [ctypes.c_void_p]),
     "pyro_batch_launch_count": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "pyro_batch_get_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
     "pyro_batch_destroy": (None, [ctypes.c_void_p]),
     "pyro_ising_sweep_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
@@ -241,6 +246,26 @@ def pyro_launch_count(h) -> int:
     return int(lib().pyro_launch_count(h))
 
 
+DEBUG_FAIL_ALLOCS, DEBUG_UNITE_BOUND = 1, 2
+
+
+def pyro_set_graphs(h, on: bool):
+    _check(lib().pyro_set_graphs(h, 1 if on else 0))
+
+
+def pyro_autotune(L: int, model: int, precision: int = FP32, beta: float = 0.2373, nsweeps: int = 3):
+    """Fastest labelling tile for this GPU and lattice (cached); returns
+    (tile, ms per sweep)."""
+    t = (ctypes.c_int * 3)()
+    ms = ctypes.c_double()
+    _check(lib().pyro_autotune(L, model, precision, beta, nsweeps, t, ctypes.byref(ms)))
+    return tuple(t), ms.value
+
+
+def pyro_debug_set(key: int, value: int):
+    _check(lib().pyro_debug_set(key, value))
+
+
 PHASES = ("local", "boundary", "flip", "measure", "accumulate")
 
 
@@ -306,6 +331,10 @@ def pyro_batch_launch_count(b) -> int:
     return int(lib().pyro_batch_launch_count(b))
 
 
+def pyro_batch_get_stream(b) -> int:
+    return lib().pyro_batch_get_stream(b) or 0
+
+
 def pyro_batch_destroy(b):
     lib().pyro_batch_destroy(b)
 
@@ -328,6 +357,8 @@ class Lattice:
                  start: str | int = "up", J: float = 1.0, tile=(0, 0, 0), stream: int | None = None):
         st = start if isinstance(start, int) else (START_RANDOM if start == "random" else START_UP)
         self.L, self.model, self.seed, self.precision = L, model, seed, precision
+        if tile == "auto":
+            tile = pyro_autotune(L, model, precision)[0]
         self.h = pyro_init_ex(L, model, seed, precision, st, J, stream, tile)
         self.N = pyro_num_sites(self.h)
 
@@ -382,6 +413,9 @@ class Lattice:
     def launches(self):
         return pyro_launch_count(self.h)
 
+    def set_graphs(self, on: bool):
+        pyro_set_graphs(self.h, on)
+
 
 class Replicas:
     """Independent lattices updated together (owns a pyro_batch)."""
@@ -425,6 +459,10 @@ class Replicas:
     @property
     def launches(self):
         return pyro_batch_launch_count(self.b)
+
+    @property
+    def stream(self) -> int:
+        return pyro_batch_get_stream(self.b)
 
 
 def replica_seed(seed: int, r: int) -> int:

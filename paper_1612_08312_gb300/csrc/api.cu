@@ -1,9 +1,14 @@
 // api.cu -- the C ABI of libpyro (include/pyro.h): argument checking, error
 // reporting and host-side layout conversion around the Engine.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "engine.h"
@@ -132,6 +137,73 @@ static int measure_of(Engine &e, int r, double *E, double *m2, double *m4)
     if (m2) *m2 = last[1];
     if (m4) *m4 = last[2];
     return PYRO_OK;
+}
+
+cudaError_t ising_set_unite_bound(int bound);
+cudaError_t vec_set_unite_bound(int bound);
+
+// ------------------------------------------------------------- autotuner --
+// Candidate tiles: powers of two, 64 to 512 cells, each edge dividing L.
+static std::vector<TileShape> tile_candidates(int L, int model)
+{
+    std::vector<TileShape> out;
+    const int edges[] = {2, 4, 8, 16, 32};
+    for (int tx : edges)
+        for (int ty : edges)
+            for (int tz : edges) {
+                const int nt = tx * ty * tz;
+                if (nt < 64 || nt > 512 || L % tx || L % ty || L % tz || ty > tx) continue;
+                if (model != PYRO_ISING && nt > 256) continue;
+                out.push_back(TileShape{tx, ty, tz});
+            }
+    return out;
+}
+
+static std::mutex tune_mutex;
+static std::map<std::tuple<std::string, int, int, int>, std::pair<TileShape, double>> tune_cache;
+
+static std::string device_name()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+    std::string n = p.name;
+    for (auto &ch : n)
+        if (ch == ' ') ch = '_';
+    return n;
+}
+
+// Optional file cache named by PYRO_AUTOTUNE_CACHE: lines
+// "<gpu> <L> <model> <precision> <TX> <TY> <TZ> <ms>".
+static bool file_lookup(const std::string &gpu, int L, int model, int prec, TileShape &t, double &ms)
+{
+    const char *path = std::getenv("PYRO_AUTOTUNE_CACHE");
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char name[256];
+    int l, m, p, tx, ty, tz;
+    double v;
+    bool found = false;
+    while (std::fscanf(f, "%255s %d %d %d %d %d %d %lf", name, &l, &m, &p, &tx, &ty, &tz, &v) == 8)
+        if (gpu == name && l == L && m == model && p == prec) {
+            t = TileShape{tx, ty, tz};
+            ms = v;
+            found = true;
+        }
+    std::fclose(f);
+    return found;
+}
+
+static void file_store(const std::string &gpu, int L, int model, int prec, const TileShape &t, double ms)
+{
+    const char *path = std::getenv("PYRO_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d %d %d %d %d %.6f\n", gpu.c_str(), L, model, prec, t.TX, t.TY, t.TZ, ms);
+    std::fclose(f);
 }
 
 }  // namespace pyro
@@ -338,6 +410,81 @@ int pyro_get_tile(pyro_handle h, int tile[3])
 
 void *pyro_get_stream(pyro_handle h) { return h ? (void *)h->e.stream : nullptr; }
 
+int pyro_set_graphs(pyro_handle h, int on)
+{
+    if (!h) return fail(PYRO_E_INVAL, "NULL handle");
+    h->e.use_graphs = on != 0;
+    return PYRO_OK;
+}
+
+int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int tile_out[3], double *ms_per_sweep)
+{
+    if (!tile_out) return fail(PYRO_E_INVAL, "NULL argument");
+    if (L < 1 || L > PYRO_MAX_L) return fail(PYRO_E_INVAL, "L must be in [1, 511]");
+    if (model < PYRO_ISING || model > PYRO_HEIS) return fail(PYRO_E_INVAL, "model must be 1, 2 or 3");
+    if (precision != PYRO_FP32 && precision != PYRO_FP64) return fail(PYRO_E_INVAL, "bad precision");
+    if (!beta_ok(beta) || nsweeps < 1) return fail(PYRO_E_INVAL, "beta must be >= 0 and nsweeps >= 1");
+    const int prec = model == PYRO_ISING ? PYRO_FP64 : precision;
+    const std::string gpu = device_name();
+    std::lock_guard<std::mutex> lock(tune_mutex);
+    const auto key = std::make_tuple(gpu, L, model, prec);
+    TileShape best = default_tile(&L, 1, model);
+    double best_ms = -1.0;
+    auto it = tune_cache.find(key);
+    if (it != tune_cache.end()) {
+        best = it->second.first;
+        best_ms = it->second.second;
+    } else if (!file_lookup(gpu, L, model, prec, best, best_ms)) {
+        for (const TileShape &t : tile_candidates(L, model)) {
+            if (!check_tile(&L, 1, model, prec, t).empty()) continue;
+            Engine e;
+            std::string err;
+            const uint64_t seed = 0x5EEDull;
+            if (e.setup(1, &L, &beta, model, prec, PYRO_START_RANDOM, 1.0, &seed, nullptr, t, err) != cudaSuccess) {
+                cudaGetLastError();
+                e.release();
+                continue;
+            }
+            e.use_graphs = false;
+            double ms = 0.0;
+            cudaError_t ce = e.sweeps(2);
+            if (ce == cudaSuccess) ce = e.time_sweeps(nsweeps, ms);
+            e.release();
+            if (ce != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (best_ms < 0.0 || ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+        if (best_ms >= 0.0) file_store(gpu, L, model, prec, best, best_ms);
+    }
+    tune_cache[key] = std::make_pair(best, best_ms);
+    tile_out[0] = best.TX;
+    tile_out[1] = best.TY;
+    tile_out[2] = best.TZ;
+    if (ms_per_sweep) *ms_per_sweep = best_ms;
+    return PYRO_OK;
+}
+
+int pyro_debug_set(int key, int64_t value)
+{
+    if (key == PYRO_DEBUG_FAIL_ALLOCS) {
+        if (value < 0) return fail(PYRO_E_INVAL, "count must be >= 0");
+        g_fail_allocs = (int)value;
+        return PYRO_OK;
+    }
+    if (key == PYRO_DEBUG_UNITE_BOUND) {
+        const int b = value <= 0 ? 0 : (value > 4096 ? 4096 : (int)value);
+        PYRO_CUDA(ising_set_unite_bound(b), "bound update");
+        PYRO_CUDA(vec_set_unite_bound(b), "bound update");
+        return PYRO_OK;
+    }
+    return fail(PYRO_E_INVAL, "unknown debug key");
+}
+
 uint64_t pyro_launch_count(pyro_handle h) { return h ? h->e.launches : 0; }
 
 int pyro_profile_phases(pyro_handle h, double beta, int n, double *phase_ms)
@@ -424,6 +571,8 @@ int64_t pyro_batch_total_sites(pyro_batch b)
 }
 
 uint64_t pyro_batch_launch_count(pyro_batch b) { return b ? b->e.launches : 0; }
+
+void *pyro_batch_get_stream(pyro_batch b) { return b ? (void *)b->e.stream : nullptr; }
 
 void pyro_batch_destroy(pyro_batch b)
 {

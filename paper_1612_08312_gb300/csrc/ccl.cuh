@@ -4,13 +4,11 @@
 // Labels are union-find parent pointers.  Linking always hangs the larger
 // root under the smaller one (atomicMin on the larger root's parent), so the
 // root of a finished cluster is its minimum index -- the canonical label.
-// Two levels:
-//   * tile-local, in shared memory, over tile-local site indices (inside a
-//     tile the local index order agrees with the global one);
-//   * global, in HBM, over global site indices of the tile-local roots of
-//     clusters that cross a tile face.
-// Every loop is bounded; exceeding a bound sets a status bit instead of
-// spinning forever.
+// This file holds the tile-local level, in shared memory, over tile-local
+// site indices (inside a tile the local index order agrees with the global
+// one); the global level for clusters that cross tile faces is in
+// sweep_core.cuh.  Every loop is bounded; exceeding a bound sets a status
+// bit instead of spinning forever.
 #pragma once
 
 #include "pyro_internal.cuh"
@@ -35,13 +33,30 @@ __device__ __forceinline__ int sfind(volatile int *lab, int x, int nt)
     return x;
 }
 
+// Root of x when no thread writes labels any more (read-only walk).
+__device__ __forceinline__ int sroot(const volatile int *lab, int x, int nt)
+{
+    int p = lab[lslot(x, nt)];
+#pragma unroll 1
+    for (int it = 0; p != x && it < 65536; ++it) {
+        x = p;
+        p = lab[lslot(x, nt)];
+    }
+    return x;
+}
+
+// Iteration bound of one union (4096).  A test can lower it (to 0) through
+// pyro_debug_set to exercise the bound-exceeded status path.
+static __constant__ int c_unite_bound = 4096;
+
 // Union of the clusters of a and b in shared memory.  Returns false if the
 // iteration bound was hit.
 __device__ __forceinline__ bool sunite(int *lab, int a, int b, int nt)
 {
     volatile int *vl = lab;
+    const int bound = c_unite_bound;
 #pragma unroll 1
-    for (int it = 0; it < 4096; ++it) {
+    for (int it = 0; it < bound; ++it) {
         a = sfind(vl, a, nt);
         b = sfind(vl, b, nt);
         if (a == b) return true;
@@ -55,69 +70,6 @@ __device__ __forceinline__ bool sunite(int *lab, int a, int b, int nt)
         b = old;  // b had been linked meanwhile: unite a with its new parent
     }
     return false;
-}
-
-// Global find through L2 (parents can be lowered by other SMs' atomics).
-__device__ __forceinline__ int gfind(const int *P, int x)
-{
-    int p = __ldcg(P + x);
-#pragma unroll 1
-    for (int it = 0; p != x && it < (1 << 20); ++it) {
-        x = p;
-        p = __ldcg(P + x);
-    }
-    return x;
-}
-
-__device__ __forceinline__ bool gunite(int *P, int a, int b)
-{
-#pragma unroll 1
-    for (int it = 0; it < 65536; ++it) {
-        a = gfind(P, a);
-        b = gfind(P, b);
-        if (a == b) return true;
-        if (a > b) {
-            const int t = a;
-            a = b;
-            b = t;
-        }
-        const int old = atomicMin(P + b, a);
-        if (old == b) return true;
-        b = old;
-    }
-    return false;
-}
-
-// Root of x once no union is in flight.
-__device__ __forceinline__ int root_of(const int *P, int x)
-{
-    int p = P[x];
-#pragma unroll 1
-    for (int it = 0; p != x && it < (1 << 20); ++it) {
-        x = p;
-        p = P[x];
-    }
-    return x;
-}
-
-// Components of a tetrahedron's four vertices under its six bond bits
-// (k = 0..5 pairs (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)): rr[v] = smallest
-// vertex connected to v.
-__device__ __forceinline__ void tet_components(uint32_t bits, int rr[4])
-{
-    rr[0] = 0;
-    rr[1] = 1;
-    rr[2] = 2;
-    rr[3] = 3;
-#pragma unroll
-    for (int pass = 0; pass < 3; ++pass)
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            if ((bits >> k) & 1u) {
-                const int m = min(rr[pair_a(k)], rr[pair_b(k)]);
-                rr[pair_a(k)] = m;
-                rr[pair_b(k)] = m;
-            }
 }
 
 // Pair index k of vertices (a, b), a < b.

@@ -135,6 +135,18 @@ void launch_accumulate(const Batch &B, bool ising, int mode, int nc, cudaStream_
 }
 
 // ------------------------------------------------------------------ host --
+int g_fail_allocs = 0;
+
+static cudaError_t engine_malloc(void **p, size_t bytes)
+{
+    if (g_fail_allocs > 0) {
+        --g_fail_allocs;
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 uint64_t ising_threshold(double beta, double J)
 {
     if (!(beta > 0.0)) return 0;
@@ -260,7 +272,7 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
                   {(void **)&p.dmask, (size_t)p.ncells * sizeof(uint32_t)},
                   {(void **)&p.st, sizeof(DevStats)}};
         for (auto &a : al) {
-            e = cudaMalloc(a.ptr, a.bytes);
+            e = engine_malloc(a.ptr, a.bytes);
             if (e != cudaSuccess) {
                 err = "device allocation failed";
                 return e;
@@ -273,13 +285,13 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
     }
     B.tile_begin[R] = ntiles;
     B.block_begin[R] = nblocks;
-    e = cudaMalloc(&B.partials, (size_t)ntiles * 4 * sizeof(double));
+    e = engine_malloc((void **)&B.partials, (size_t)ntiles * 4 * sizeof(double));
     if (e != cudaSuccess) {
         err = "device allocation failed";
         return e;
     }
     owned.push_back(B.partials);
-    e = cudaMalloc(&d_reps, (size_t)R * sizeof(Rep));
+    e = engine_malloc((void **)&d_reps, (size_t)R * sizeof(Rep));
     if (e != cudaSuccess) {
         err = "device allocation failed";
         return e;
@@ -487,6 +499,28 @@ cudaError_t Engine::sweeps(int n)
     sweep += n;
     labels_valid = true;
     return cudaGetLastError();
+}
+
+cudaError_t Engine::time_sweeps(int n, double &ms)
+{
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+    }
+    cudaEventRecord(a, stream);
+    e = sweeps(n);
+    cudaEventRecord(b, stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float f = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&f, a, b);
+    ms = n > 0 ? (double)f / n : 0.0;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
 }
 
 cudaError_t Engine::measure()

@@ -47,6 +47,8 @@ struct Engine {
     cudaError_t set_sweep(uint64_t s);
     cudaError_t set_trace(int r, int64_t cap);
     cudaError_t compute_labels();
+    // mean device ms per sweep over n separately launched sweeps
+    cudaError_t time_sweeps(int n, double &ms);
     cudaError_t guard_epoch(int n);
     int read_status(std::string &err);
     int launches_per_sweep() const;
@@ -59,6 +61,10 @@ struct Engine {
 };
 
 uint64_t ising_threshold(double beta, double J);
+
+// Test hooks (pyro_debug_set): the next `fail_allocs` device allocations
+// of an engine set-up report failure.
+extern int g_fail_allocs;
 TileShape default_tile(const int *Ls, int R, int model);
 std::string check_tile(const int *Ls, int R, int model, int prec, const TileShape &t);
 size_t local_smem(int model, int prec, const TileShape &t);

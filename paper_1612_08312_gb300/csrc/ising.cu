@@ -114,15 +114,20 @@ __global__ void __launch_bounds__(512) labels_kernel(const __grid_constant__ Bat
 // tile, written to the tile's partial slot.
 __global__ void __launch_bounds__(512) ising_measure_kernel(const __grid_constant__ Batch B)
 {
-    extern __shared__ __align__(16) int smem[];
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
-    uint16_t *hs = reinterpret_cast<uint16_t *>(smem);
-    stage_spin_halo(c, static_cast<const uint16_t *>(R.spins), hs);
-    __syncthreads();
+    const uint16_t *spins = static_cast<const uint16_t *>(R.spins);
+    const int L = c.L;
+    const int x = c.ox + c.lx, y = c.oy + c.ly, z = c.oz + c.lz;
     uint32_t w[7];
-    cell_words(c, hs, w);
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+        const int cx = (m & 1) ? wrap_back(x, L) : x;
+        const int cy = (m & 2) ? wrap_back(y, L) : y;
+        const int cz = (m & 4) ? wrap_back(z, L) : z;
+        w[m] = spins[(int64_t)cx + (int64_t)L * ((int64_t)cy + (int64_t)L * cz)];
+    }
     uint32_t A, Bg, C;
     antiparallel_groups(w[0], down_word(w), A, Bg, C);
     const unsigned mask = lanes_mask(c.nt);
@@ -163,19 +168,28 @@ __global__ void __launch_bounds__(CELL_BLOCK) ising_init_kernel(const __grid_con
     static_cast<uint16_t *>(R.spins)[cell] = (uint16_t)word;
 }
 
-// Unite the clusters joined by the union pairs that leave each tile, and
-// mark both tile-local roots as crossing (bit 15 of their L16 entry).
-// Model-independent: used by the n-vector sweeps too.
+// Phase 1, over the face cells of every tile (one thread each): FLATTEN =
+// false unites the clusters joined by the union pairs that leave the tile
+// and marks both tile-local roots as crossing (bit 15 of their L16 entry);
+// FLATTEN = true then points every crossing root straight at its cluster
+// root.  Model-independent: used by the n-vector sweeps too.
+template <bool FLATTEN>
 __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ Batch B)
 {
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
-    const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
-    if (!(c.lx == 0 || c.ly == 0 || c.lz == 0)) return;
-    uint32_t todo = R.dmask[c.cell];
+    const int nface = face_cells(B.TX, B.TY, B.TZ);
+    if ((int)threadIdx.x >= nface) return;
+    int lx, ly, lz;
+    face_cell_coords(B, threadIdx.x, lx, ly, lz);
+    const int64_t tile = blockIdx.x - B.tile_begin[r];
+    const int64_t txy = tile / R.ntx;
+    const int L = R.L;
+    const int x = (int)(tile - txy * R.ntx) * B.TX + lx;
+    const int y = (int)(txy % R.nty) * B.TY + ly;
+    const int z = (int)(txy / R.nty) * B.TZ + lz;
+    uint32_t todo = R.dmask[(int64_t)x + (int64_t)L * ((int64_t)y + (int64_t)L * z)];
     if (!todo) return;
-    const int L = c.L;
-    const int x = c.ox + c.lx, y = c.oy + c.ly, z = c.oz + c.lz;
     const uint32_t stamp = (uint32_t)R.st->epoch;
     unsigned long long *P = R.P;
     unsigned *Lw = reinterpret_cast<unsigned *>(R.L16);
@@ -193,15 +207,31 @@ __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ B
             const int cy = (m & 2) ? wrap_back(y, L) : y;
             const int cz = (m & 4) ? wrap_back(z, L) : z;
             g[e] = crossing_root(R, B, cx, cy, cz, down_bit(f, v));
-            const unsigned bitm = 1u << (15 + 16 * (g[e] & 1));
-            if (!(__ldcg(Lw + (g[e] >> 1)) & bitm)) atomicOr(Lw + (g[e] >> 1), bitm);
         }
-        ok &= punite(P, g[0], g[1], stamp);
+        if (!FLATTEN) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const unsigned bitm = 1u << (15 + 16 * (g[e] & 1));
+                if (!(__ldcg(Lw + (g[e] >> 1)) & bitm)) atomicOr(Lw + (g[e] >> 1), bitm);
+            }
+            ok &= punite(P, g[0], g[1], stamp);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int rt = pfind(P, g[e], stamp);
+                if (rt != g[e]) {
+                    const unsigned long long nv = ((unsigned long long)stamp << 32) | (uint32_t)rt;
+                    if (__ldcg(P + g[e]) != nv) __stcg(P + g[e], nv);
+                }
+            }
+        }
     }
     if (!ok) atomicOr(&R.st->status, ST_NOCONVERGE);
 }
 
 // ------------------------------------------------------------ launchers --
+cudaError_t ising_set_unite_bound(int bound) { return cudaMemcpyToSymbol(c_unite_bound, &bound, sizeof(int)); }
+
 static size_t halo_spin_bytes(const TileShape &t) { return (size_t)halo_cells(t.TX, t.TY, t.TZ) * sizeof(uint16_t); }
 
 size_t ising_local_smem(const TileShape &t) { return core_smem_bytes(t.TX * t.TY * t.TZ) + halo_spin_bytes(t); }
@@ -210,12 +240,11 @@ size_t resolve_smem(const TileShape &t) { return resolve_smem_bytes(t.TX * t.TY 
 
 cudaError_t ising_prepare(const TileShape &t)
 {
-    cudaError_t e = cudaFuncSetAttribute(ising_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ising_local_smem(t));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ising_flip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)resolve_smem(t));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(labels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)resolve_smem(t));
+    const int mx = smem_optin();
+    if ((int)ising_local_smem(t) > mx || (int)resolve_smem(t) > mx) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(ising_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ising_flip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(labels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return e;
 }
 
@@ -226,7 +255,10 @@ void ising_launch_init(const Batch &B, int64_t nblocks, int random, cudaStream_t
 
 void launch_boundary(const Batch &B, int64_t ntiles, cudaStream_t s)
 {
-    boundary_kernel<<<(unsigned)ntiles, B.TX * B.TY * B.TZ, 0, s>>>(B);
+    const int nf = face_cells(B.TX, B.TY, B.TZ);
+    const int threads = (nf + 31) & ~31;
+    boundary_kernel<false><<<(unsigned)ntiles, threads, 0, s>>>(B);
+    boundary_kernel<true><<<(unsigned)ntiles, threads, 0, s>>>(B);
 }
 
 void launch_labels(const Batch &B, int64_t ntiles, cudaStream_t s)
@@ -247,8 +279,7 @@ void ising_launch_phase(int p, const Batch &B, int64_t ntiles, cudaStream_t s)
 
 void ising_launch_measure(const Batch &B, int64_t ntiles, cudaStream_t s)
 {
-    const TileShape t{B.TX, B.TY, B.TZ};
-    ising_measure_kernel<<<(unsigned)ntiles, B.TX * B.TY * B.TZ, halo_spin_bytes(t), s>>>(B);
+    ising_measure_kernel<<<(unsigned)ntiles, B.TX * B.TY * B.TZ, 0, s>>>(B);
 }
 
 }  // namespace pyro

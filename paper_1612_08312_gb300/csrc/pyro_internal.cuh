@@ -165,4 +165,16 @@ namespace pyro {
 // Thread-local last-error message.
 void set_error(const std::string &msg);
 
+// Largest dynamic shared memory a block may opt into on the current device.
+// Kernels' MaxDynamicSharedMemorySize attributes are set to this value (a
+// per-function setting that must never be lowered below what another
+// lattice's tile needs).
+inline int smem_optin()
+{
+    int dev = 0, v = 48 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
 }  // namespace pyro

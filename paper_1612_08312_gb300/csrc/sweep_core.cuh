@@ -243,15 +243,35 @@ __device__ __forceinline__ uint32_t cell_flip_bits(const TileCtx &c, uint64_t se
 
 // --------------------------------------------------- tile-local labelling --
 // Shared memory of the local kernels: labels (16 nt ints), union pairs
-// (12 nt words), pair counter, tetrahedron table (64 bytes); the model's
-// staging area follows.
-__host__ __device__ constexpr size_t core_smem_bytes(int nt) { return (size_t)28 * nt * 4 + 16 + 64; }
+// (12 nt words), three pair counters, tetrahedron table (64 x 16 bits); the
+// model's staging area follows.
+__host__ __device__ constexpr size_t core_smem_bytes(int nt) { return (size_t)28 * nt * 4 + 16 + 128; }
+
+// Union round of the down-tetrahedron pair k of FCC point f: the pair's two
+// cells differ along the axes of m = mask(a) ^ mask(b).  Round 0: same cell
+// or x only; round 1: y without z; round 2: z.  After each round every
+// component representative is pointed straight at its root, so the finds
+// of the next round start from depth one.
+__host__ __device__ constexpr int pair_round(int f, int k)
+{
+    return ((down_mask(f, pair_a(k)) ^ down_mask(f, pair_b(k))) & 4) ? 2
+         : ((down_mask(f, pair_a(k)) ^ down_mask(f, pair_b(k))) & 2) ? 1 : 0;
+}
+
+__host__ __device__ constexpr uint32_t round_mask(int r)
+{
+    uint32_t m = 0;
+    for (int f = 0; f < 4; ++f)
+        for (int k = 0; k < 6; ++k)
+            if (pair_round(f, k) == r) m |= 1u << (6 * f + k);
+    return m;
+}
 
 struct CoreSmem {
     int *lab;
     uint32_t *plist;
     int *pcount;
-    uint8_t *lut;
+    uint16_t *lut;   // tetrahedron table: 8 bits of smallest vertices, 4 bits of representatives
     unsigned char *stage;  // model staging area (16-byte aligned)
 };
 
@@ -260,18 +280,28 @@ __device__ __forceinline__ CoreSmem core_smem(int *smem, int nt)
     CoreSmem s;
     s.lab = smem;
     s.plist = reinterpret_cast<uint32_t *>(smem + 16 * nt);
-    s.pcount = smem + 28 * nt;
-    s.lut = reinterpret_cast<uint8_t *>(smem + 28 * nt + 4);
-    s.stage = reinterpret_cast<unsigned char *>(smem + 28 * nt + 20);
+    s.pcount = smem + 28 * nt;  // three counters
+    s.lut = reinterpret_cast<uint16_t *>(smem + 28 * nt + 4);
+    s.stage = reinterpret_cast<unsigned char *>(smem + 28 * nt + 4 + 32);
     return s;
 }
 
 // Called by every thread before the model's staging (covered by the same
-// __syncthreads): clears the pair counter and fills the table.
+// __syncthreads): clears the pair counters and fills the table.
 __device__ __forceinline__ void core_prologue(const CoreSmem &s)
 {
-    if (threadIdx.x == 0) *s.pcount = 0;
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) s.lut[i] = (uint8_t)tet_table_entry((uint32_t)i);
+    if (threadIdx.x == 0) {  // the block may have fewer than three threads
+        s.pcount[0] = 0;
+        s.pcount[1] = 0;
+        s.pcount[2] = 0;
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        const uint32_t e = tet_table_entry((uint32_t)i);
+        uint32_t reps = 0;
+        for (int v = 0; v < 4; ++v)
+            if (((e >> (2 * v)) & 3u) == (uint32_t)v) reps |= 1u << v;
+        s.lut[i] = (uint16_t)(e | (reps << 8));
+    }
 }
 
 // Tile-local labelling of one cell's sites from its active-bond groups.
@@ -283,10 +313,13 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
                                            uint32_t C, uint32_t sweep)
 {
     const int nt = c.nt;
+    const uint32_t out = (c.bx ? 1u : 0u) | (c.by ? 2u : 0u) | (c.bz ? 4u : 0u);  // axes whose backward step leaves
     uint32_t uptab[4];
+    uint32_t reps = 0;  // bit 4 f + v: site is its up-tetrahedron component's representative
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         uptab[f] = s.lut[up_tet_index(A, Bg, f)];
+        reps |= ((uptab[f] >> 8) & 0xFu) << (4 * f);
 #pragma unroll
         for (int v = 0; v < 4; ++v)
             s.lab[lslot(16 * c.t + 4 * f + v, nt)] = 16 * c.t + 4 * f + (int)((uptab[f] >> (2 * v)) & 3u);
@@ -300,38 +333,53 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
             const int rv = (int)((dt >> (2 * v)) & 3u);
             if (rv == v) continue;
             const int k = pair_index(rv, v);
-            // rv < v; both vertices of the pair must lie in the tile
-            bool inside = vertex_inside(c, down_mask(f, v));
+            bool inside = !(down_mask(f, v) & out);
 #pragma unroll
             for (int u = 0; u < 3; ++u)
-                if (rv == u) inside = inside && vertex_inside(c, down_mask(f, u));
+                if (rv == u) inside = inside && !(down_mask(f, u) & out);
             if (inside) inpairs |= 1u << (6 * f + k);
             else cross |= 1u << (6 * f + k);
         }
     }
-    __syncthreads();  // labels initialised
-    const int n = __popc(inpairs);
-    int base = n ? atomicAdd(s.pcount, n) : 0;
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            if ((inpairs >> (6 * f + k)) & 1u) {
-                const int va = pair_a(k), vb = pair_b(k);
-                const int a = 16 * vertex_local_cell(c, down_mask(f, va)) + down_bit(f, va);
-                const int b = 16 * vertex_local_cell(c, down_mask(f, vb)) + down_bit(f, vb);
-                s.plist[base++] = (uint32_t)a | ((uint32_t)b << 16);
-            }
-    __syncthreads();
-    const int np = *s.pcount;
     bool ok = true;
-    for (int e = threadIdx.x; e < np; e += nt) {
-        const uint32_t pr = s.plist[e];
-        ok &= sunite(s.lab, (int)(pr & 0xFFFFu), (int)(pr >> 16), nt);
+#pragma unroll
+    for (int rnd = 0; rnd < 3; ++rnd) {
+        __syncthreads();  // labels initialised / previous round flattened
+        const uint32_t mine = inpairs & round_mask(rnd);
+        const int n = __popc(mine);
+        int base = n ? atomicAdd(s.pcount + rnd, n) : 0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                if (pair_round(f, k) == rnd && ((mine >> (6 * f + k)) & 1u)) {
+                    const int va = pair_a(k), vb = pair_b(k);
+                    const int a = 16 * vertex_local_cell(c, down_mask(f, va)) + down_bit(f, va);
+                    const int b = 16 * vertex_local_cell(c, down_mask(f, vb)) + down_bit(f, vb);
+                    s.plist[base++] = (uint32_t)a | ((uint32_t)b << 16);
+                }
+        __syncthreads();
+        const int np = s.pcount[rnd];
+        for (int e = threadIdx.x; e < np; e += nt) {
+            const uint32_t pr = s.plist[e];
+            ok &= sunite(s.lab, (int)(pr & 0xFFFFu), (int)(pr >> 16), nt);
+        }
+        __syncthreads();
+        // point this cell's component representatives straight at their roots
+#pragma unroll
+        for (int sb = 0; sb < 16; ++sb)
+            if ((reps >> sb) & 1u) {
+                const int x = 16 * c.t + sb;
+                const int r = sfind(s.lab, x, nt);
+                s.lab[lslot(x, nt)] = r;
+            }
     }
     if (!ok) atomicOr(&R.st->status, ST_NOCONVERGE);
     __syncthreads();
-    // resolve: one find per up-tetrahedron component, shared by its sites
+    // every site takes the root of its up-tetrahedron representative.  A
+    // representative's entry may have been reset to an older ancestor by
+    // another thread's path halving after it was flattened, so follow it to
+    // the root (no label changes any more: a read-only walk).
     uint32_t packed[8];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
@@ -343,7 +391,7 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
 #pragma unroll
             for (int u = 0; u < v; ++u)
                 if (rv == (uint32_t)u) r = root[u];
-            if (rv == (uint32_t)v) r = (uint32_t)sfind(s.lab, 16 * c.t + 4 * f + v, nt);
+            if (rv == (uint32_t)v) r = (uint32_t)sroot(s.lab, 16 * c.t + 4 * f + v, nt);
             root[v] = r;
         }
         packed[2 * f] = root[0] | (root[1] << 16);
@@ -422,61 +470,74 @@ __device__ __forceinline__ int crossing_root(const Rep &R, const Batch &B, int x
     return 16 * (rx + L * (ry + L * rz)) + (lr & 15);
 }
 
-// Shared-memory bytes of the resolve stage: the global root of each
-// crossing tile-local root (16 nt ints, slot layout), the tile's L16 entries
-// (slot layout) and flip words.
-__host__ __device__ constexpr size_t resolve_smem_bytes(int nt)
-{
-    return (size_t)16 * nt * 4 + (size_t)16 * nt * 2 + (size_t)nt * 2 + 16;
-}
+// Shared-memory bytes of the resolve stage: the tile's L16 entries (slot
+// layout) and flip words.
+__host__ __device__ constexpr size_t resolve_smem_bytes(int nt) { return (size_t)16 * nt * 2 + (size_t)nt * 2 + 16; }
 
 // Resolve every site of the calling thread's cell to the global index of
 // its cluster's root and the root's flip bit.  Stages the tile's L16 and F
 // words in shared memory; roots of clusters that stay inside the tile are
-// final; each crossing tile-local root is looked up in P once, by the
-// thread that owns it.  stamp: the links' sweep stamp.  Called by every
-// thread of the block.
+// final, the others are looked up in P (flattened: one or two hops).
+// stamp: the links' sweep stamp.  Called by every thread of the block.
 __device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, int *smem, uint32_t stamp, int root[16],
                                              uint32_t &flip)
 {
     const int nt = c.nt;
-    int *groot = smem;
-    uint16_t *ls = reinterpret_cast<uint16_t *>(smem + 16 * nt);
+    uint16_t *ls = reinterpret_cast<uint16_t *>(smem);
     uint16_t *fs = ls + 16 * nt;
     const uint4 *src = reinterpret_cast<const uint4 *>(R.L16 + 16 * c.cell);
     const uint4 a0 = src[0], a1 = src[1];
     const uint32_t w[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    // global index of each site's tile-local root
-    int g[16];
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
-        const uint32_t e = (w[s >> 1] >> (16 * (s & 1))) & 0xFFFFu;
-        ls[lslot(16 * c.t + s, nt)] = (uint16_t)e;
-        const int lr = (int)(e & 0x7FFFu);
-        const int lc = lr >> 4;
-        const int rx = c.ox + (lc & (c.TX - 1));
-        const int ry = c.oy + ((lc >> c.lTX) & (c.TY - 1));
-        const int rz = c.oz + (lc >> (c.lTX + c.lTY));
-        g[s] = 16 * (rx + c.L * (ry + c.L * rz)) + (lr & 15);
-        // a crossing root (its own entry is flagged) is resolved here
-        if ((e & 0x8000u) && lr == 16 * c.t + s) groot[lslot(lr, nt)] = proot(R.P, g[s], stamp);
-    }
+    for (int s = 0; s < 16; ++s) ls[lslot(16 * c.t + s, nt)] = (uint16_t)(w[s >> 1] >> (16 * (s & 1)));
     fs[c.t] = R.F[c.cell];
     __syncthreads();
     flip = 0;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
         const int lr = (int)((w[s >> 1] >> (16 * (s & 1))) & 0x7FFFu);
+        const int lc = lr >> 4;
+        const int rx = c.ox + (lc & (c.TX - 1));
+        const int ry = c.oy + ((lc >> c.lTX) & (c.TY - 1));
+        const int rz = c.oz + (lc >> (c.lTX + c.lTY));
+        int g = 16 * (rx + c.L * (ry + c.L * rz)) + (lr & 15);
         uint32_t fb;
-        int r = g[s];
         if (ls[lslot(lr, nt)] & 0x8000u) {
-            r = groot[lslot(lr, nt)];
-            fb = (R.F[r >> 4] >> (r & 15)) & 1u;
+            g = proot(R.P, g, stamp);
+            fb = (R.F[g >> 4] >> (g & 15)) & 1u;
         } else {
-            fb = (fs[lr >> 4] >> (lr & 15)) & 1u;
+            fb = (fs[lc] >> (lr & 15)) & 1u;
         }
-        root[s] = r;
+        root[s] = g;
         flip |= fb << s;
+    }
+}
+
+// ------------------------------------------------------- face-cell grid --
+// Cells of a tile with lx == 0, ly == 0 or lz == 0 (the cells that own the
+// tetrahedra leaving the tile), enumerated compactly: the lz == 0 plane,
+// then for each lz > 0 the row ly == 0 and the column lx == 0.
+__host__ __device__ constexpr int face_cells(int TX, int TY, int TZ) { return TX * TY * TZ - (TX - 1) * (TY - 1) * (TZ - 1); }
+
+__device__ __forceinline__ void face_cell_coords(const Batch &B, int i, int &lx, int &ly, int &lz)
+{
+    const int plane = B.TX * B.TY;
+    if (i < plane) {
+        lz = 0;
+        ly = i >> B.lTX;
+        lx = i & (B.TX - 1);
+        return;
+    }
+    const int per = B.TX + B.TY - 1;
+    const int j = i - plane;
+    lz = 1 + j / per;
+    const int k = j - (lz - 1) * per;
+    if (k < B.TX) {
+        ly = 0;
+        lx = k;
+    } else {
+        ly = k - B.TX + 1;
+        lx = 0;
     }
 }
 

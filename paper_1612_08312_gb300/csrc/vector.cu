@@ -295,6 +295,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) vec_init_kernel(const __grid_const
 }
 
 // ------------------------------------------------------------ launchers --
+cudaError_t vec_set_unite_bound(int bound) { return cudaMemcpyToSymbol(c_unite_bound, &bound, sizeof(int)); }
+
 size_t resolve_smem(const TileShape &t);
 void launch_boundary(const Batch &B, int64_t ntiles, cudaStream_t s);
 
@@ -310,11 +312,10 @@ template <int NC, typename T>
 struct VecOps {
     static cudaError_t prepare(const TileShape &t, int prec)
     {
-        cudaError_t e = cudaFuncSetAttribute(vec_local_kernel<NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)vec_local_smem(t, prec));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(vec_flip_kernel<NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)resolve_smem(t));
+        const int mx = smem_optin();
+        if ((int)vec_local_smem(t, prec) > mx || (int)resolve_smem(t) > mx) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(vec_local_kernel<NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(vec_flip_kernel<NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         return e;
     }
     static void init(const Batch &B, int64_t nblocks, int random, cudaStream_t s)
@@ -345,8 +346,13 @@ struct VecOps {
         }                                                                           \
     } while (0)
 
+cudaError_t ising_prepare(const TileShape &t);
+
 cudaError_t vec_prepare(int model, int prec, const TileShape &t)
 {
+    // the labels kernel (compiled with the Ising sweep) serves every model
+    const cudaError_t e = ising_prepare(t);
+    if (e != cudaSuccess) return e;
     if (model == PYRO_XY) return prec == PYRO_FP64 ? VecOps<2, double>::prepare(t, prec) : VecOps<2, float>::prepare(t, prec);
     return prec == PYRO_FP64 ? VecOps<3, double>::prepare(t, prec) : VecOps<3, float>::prepare(t, prec);
 }

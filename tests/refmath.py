@@ -221,6 +221,20 @@ def bond_rng_ids(nbonds: int) -> np.ndarray:
     return (48 * (r >> 2) + 16 * RNG_G[k] + 4 * (r & 3) + RNG_Q[k]).astype(np.uint64)
 
 
+def bond_rng_ids_of(b: np.ndarray) -> np.ndarray:
+    b = np.asarray(b, dtype=np.int64)
+    r, k = b // 12, b % 12
+    return (48 * (r >> 2) + 16 * RNG_G[k] + 4 * (r & 3) + RNG_Q[k]).astype(np.uint64)
+
+
+def bond_words_of(seed: int, sweep: int, bonds: np.ndarray) -> np.ndarray:
+    """32-bit uniforms of the given bonds 12 r + k."""
+    ids = bond_rng_ids_of(bonds)
+    hi = stream_bytes(seed, sweep, 1, ids).astype(np.uint64)
+    lo = stream_words(seed, sweep, 5, ids).astype(np.uint64) & np.uint64(0xFFFFFF)
+    return (hi << np.uint64(24)) | lo
+
+
 def bond_words(seed: int, sweep: int, nbonds: int) -> np.ndarray:
     """32-bit uniform of each bond 12 r + k: its id's BOND-stream byte as the
     top 8 bits, the low 24 bits of its TIE-stream word (tag 5) below."""

@@ -80,3 +80,11 @@ def test_batch_rejects_bad_arguments():
         with pytest.raises(pyro.PyroError) as ei:
             pyro.pyro_batch_init(Ls, betas, pyro.ISING)
         assert ei.value.code == pyro.E_INVAL
+
+
+def test_debug_hook_rejects_bad_keys_without_a_gpu():
+    with pytest.raises(pyro.PyroError):
+        pyro.pyro_debug_set(99, 1)
+    with pytest.raises(pyro.PyroError):
+        pyro.pyro_debug_set(pyro.DEBUG_FAIL_ALLOCS, -1)
+    pyro.pyro_debug_set(pyro.DEBUG_FAIL_ALLOCS, 0)

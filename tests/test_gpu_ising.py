@@ -54,6 +54,12 @@ def test_l24_many_tiles():
     run_pair(24, 4.21394, seed=5, start="random", sweeps=3)
 
 
+def test_l48_many_sweeps_near_tc():
+    # 216 tiles of 512 cells, every sweep compared (rare interleavings of
+    # the shared-memory union-find must never change a label)
+    run_pair(48, 4.21394, seed=17, start="random", sweeps=8)
+
+
 def test_tile_over_512_cells_is_rejected():
     with pytest.raises(pyro.PyroError) as ei:
         pyro.Lattice(16, pyro.ISING, 1, tile=(16, 16, 4))
