@@ -180,10 +180,11 @@ uint64_t pyro_launch_count(pyro_handle h);
  * with a library-owned stream).  Off = one launch per phase per sweep. */
 int pyro_set_graphs(pyro_handle h, int on);
 
-/* Autotuner: time every candidate labelling tile (power-of-two edges
- * dividing L, 64 to 512 cells) on a scratch lattice for nsweeps sweeps at
- * beta and return the fastest in tile_out (pass it in pyro_config.tile) and
- * its device ms per sweep (NULL allowed).  Results are cached per (GPU
+/* Autotuner: equilibrate a scratch lattice for 60 sweeps at beta, then
+ * replay the same nsweeps sweeps from that state with every candidate
+ * labelling tile (power-of-two edges dividing L, 64 to 512 cells) and
+ * return the fastest in tile_out (pass it in pyro_config.tile) and its
+ * device ms per sweep (NULL allowed).  Results are cached per (GPU
  * name, L, model, precision) in the process and, if the environment
  * variable PYRO_AUTOTUNE_CACHE names a file, across processes.  Allocates
  * and frees a scratch lattice per candidate; synchronises the device. */

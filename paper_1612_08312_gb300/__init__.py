@@ -253,7 +253,7 @@ def pyro_set_graphs(h, on: bool):
     _check(lib().pyro_set_graphs(h, 1 if on else 0))
 
 
-def pyro_autotune(L: int, model: int, precision: int = FP32, beta: float = 0.2373, nsweeps: int = 3):
+def pyro_autotune(L: int, model: int, precision: int = FP32, beta: float = 0.2373, nsweeps: int = 5):
     """Fastest labelling tile for this GPU and lattice (cached); returns
     (tile, ms per sweep)."""
     t = (ctypes.c_int * 3)()

@@ -435,11 +435,23 @@ int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int
         best = it->second.first;
         best_ms = it->second.second;
     } else if (!file_lookup(gpu, L, model, prec, best, best_ms)) {
+        // Equilibrate one lattice with the default tile, then replay the same
+        // sweeps from that state with every candidate tile: the chain does
+        // not depend on the tile, so every candidate does identical work.
+        const uint64_t seed = 0x5EEDull;
+        const int warm = 60;
+        Engine ref;
+        std::string err;
+        const TileShape t0 = default_tile(&L, 1, model);
+        if (ref.setup(1, &L, &beta, model, prec, PYRO_START_RANDOM, 1.0, &seed, nullptr, t0, err) != cudaSuccess ||
+            ref.sweeps(warm) != cudaSuccess || cudaStreamSynchronize(ref.stream) != cudaSuccess) {
+            cudaGetLastError();
+            ref.release();
+            return fail(PYRO_E_CUDA, "autotune: reference lattice failed");
+        }
         for (const TileShape &t : tile_candidates(L, model)) {
             if (!check_tile(&L, 1, model, prec, t).empty()) continue;
             Engine e;
-            std::string err;
-            const uint64_t seed = 0x5EEDull;
             if (e.setup(1, &L, &beta, model, prec, PYRO_START_RANDOM, 1.0, &seed, nullptr, t, err) != cudaSuccess) {
                 cudaGetLastError();
                 e.release();
@@ -447,7 +459,10 @@ int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int
             }
             e.use_graphs = false;
             double ms = 0.0;
-            cudaError_t ce = e.sweeps(2);
+            cudaError_t ce = cudaMemcpyAsync(e.reps[0].spins, ref.reps[0].spins, ref.spin_bytes(0),
+                                             cudaMemcpyDeviceToDevice, e.stream);
+            if (ce == cudaSuccess) ce = e.set_sweep(ref.sweep);
+            if (ce == cudaSuccess) ce = e.sweeps(1);
             if (ce == cudaSuccess) ce = e.time_sweeps(nsweeps, ms);
             e.release();
             if (ce != cudaSuccess) {
@@ -459,6 +474,7 @@ int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int
                 best = t;
             }
         }
+        ref.release();
         if (best_ms >= 0.0) file_store(gpu, L, model, prec, best, best_ms);
     }
     tune_cache[key] = std::make_pair(best, best_ms);
