@@ -88,9 +88,7 @@ __global__ void __launch_bounds__(512) ising_flip_kernel(const __grid_constant__
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
-    int root[16];
-    uint32_t flip;
-    resolve_cell(c, R, smem, (uint32_t)R.st->epoch, root, flip);
+    const uint32_t flip = cell_flip_mask(c, R, smem);
     uint16_t *spins = static_cast<uint16_t *>(R.spins);
     spins[c.cell] = (uint16_t)((uint32_t)spins[c.cell] ^ flip);
 }
@@ -172,7 +170,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) ising_init_kernel(const __grid_con
 // false unites the clusters joined by the union pairs that leave the tile
 // and marks both tile-local roots as crossing (bit 15 of their L16 entry);
 // FLATTEN = true then points every crossing root straight at its cluster
-// root.  Model-independent: used by the n-vector sweeps too.
+// root and copies the cluster's flip bit into bit 14 of the crossing root's
+// entry.  Model-independent: used by the n-vector sweeps too.
 template <bool FLATTEN>
 __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ Batch B)
 {
@@ -222,6 +221,12 @@ __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ B
                 if (rt != g[e]) {
                     const unsigned long long nv = ((unsigned long long)stamp << 32) | (uint32_t)rt;
                     if (__ldcg(P + g[e]) != nv) __stcg(P + g[e], nv);
+                }
+                // the cluster's flip bit, kept in bit 14 of the crossing
+                // root's own entry for the flip kernel
+                if ((R.F[rt >> 4] >> (rt & 15)) & 1u) {
+                    const unsigned bitm = 1u << (14 + 16 * (g[e] & 1));
+                    if (!(__ldcg(Lw + (g[e] >> 1)) & bitm)) atomicOr(Lw + (g[e] >> 1), bitm);
                 }
             }
         }

@@ -462,7 +462,7 @@ __device__ __forceinline__ int proot(const unsigned long long *P, int x, uint32_
 __device__ __forceinline__ int crossing_root(const Rep &R, const Batch &B, int x, int y, int z, int s)
 {
     const int L = R.L;
-    const int lr = R.L16[16 * ((int64_t)x + (int64_t)L * ((int64_t)y + (int64_t)L * z)) + s] & 0x7FFF;
+    const int lr = R.L16[16 * ((int64_t)x + (int64_t)L * ((int64_t)y + (int64_t)L * z)) + s] & 0x1FFF;
     const int lc = lr >> 4;
     const int rx = (x & ~(B.TX - 1)) + (lc & (B.TX - 1));
     const int ry = (y & ~(B.TY - 1)) + ((lc >> B.lTX) & (B.TY - 1));
@@ -495,7 +495,7 @@ __device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, int
     flip = 0;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
-        const int lr = (int)((w[s >> 1] >> (16 * (s & 1))) & 0x7FFFu);
+        const int lr = (int)((w[s >> 1] >> (16 * (s & 1))) & 0x1FFFu);
         const int lc = lr >> 4;
         const int rx = c.ox + (lc & (c.TX - 1));
         const int ry = c.oy + ((lc >> c.lTX) & (c.TY - 1));
@@ -511,6 +511,35 @@ __device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, int
         root[s] = g;
         flip |= fb << s;
     }
+}
+
+// Flip mask of the calling thread's cell (bit s = site 16 c + s flips).
+// Stages the tile's L16 and F words in shared memory.  A site's cluster
+// either stays inside the tile (its flip bit is the tile-local root's bit
+// of F) or crosses a face (its tile-local root's entry carries the cluster's
+// flip bit in bit 14, written by the crossing flatten pass).  No global
+// lookups.  Called by every thread of the block.
+__device__ __forceinline__ uint32_t cell_flip_mask(const TileCtx &c, const Rep &R, int *smem)
+{
+    const int nt = c.nt;
+    uint16_t *ls = reinterpret_cast<uint16_t *>(smem);
+    uint16_t *fs = ls + 16 * nt;
+    const uint4 *src = reinterpret_cast<const uint4 *>(R.L16 + 16 * c.cell);
+    const uint4 a0 = src[0], a1 = src[1];
+    const uint32_t w[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+    for (int s = 0; s < 16; ++s) ls[lslot(16 * c.t + s, nt)] = (uint16_t)(w[s >> 1] >> (16 * (s & 1)));
+    fs[c.t] = R.F[c.cell];
+    __syncthreads();
+    uint32_t flip = 0;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int lr = (int)((w[s >> 1] >> (16 * (s & 1))) & 0x1FFFu);
+        const uint32_t re = ls[lslot(lr, nt)];
+        const uint32_t fb = (re & 0x8000u) ? ((re >> 14) & 1u) : ((fs[lr >> 4] >> (lr & 15)) & 1u);
+        flip |= fb << s;
+    }
+    return flip;
 }
 
 // ------------------------------------------------------- face-cell grid --

@@ -190,9 +190,7 @@ __global__ void __launch_bounds__(512) vec_flip_kernel(const __grid_constant__ B
     const int rep = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[rep];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[rep]);
-    int root[16];
-    uint32_t flip;
-    resolve_cell(c, R, smem, (uint32_t)R.st->epoch, root, flip);
+    uint32_t flip = cell_flip_mask(c, R, smem);
     if (!flip) return;
     double rd[3];
     unit_vector_dev<NC>(R.seed, (uint32_t)R.st->sweep, TAG_AXIS, 0, rd);
