@@ -96,13 +96,12 @@ __global__ void __launch_bounds__(512) ising_flip_kernel(const __grid_constant__
 // Canonical label (global index of the cluster root) of every site.
 __global__ void __launch_bounds__(512) labels_kernel(const __grid_constant__ Batch B)
 {
-    extern __shared__ __align__(16) int smem[];
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
     int root[16];
     uint32_t flip;
-    resolve_cell(c, R, smem, (uint32_t)R.st->last_epoch, root, flip);
+    resolve_cell(c, R, (uint32_t)R.st->last_epoch, root, flip);
     int4 *dst = reinterpret_cast<int4 *>(R.labels + 16 * c.cell);
 #pragma unroll
     for (int q = 0; q < 4; ++q) dst[q] = make_int4(root[4 * q], root[4 * q + 1], root[4 * q + 2], root[4 * q + 3]);
@@ -167,11 +166,11 @@ __global__ void __launch_bounds__(CELL_BLOCK) ising_init_kernel(const __grid_con
 }
 
 // Phase 1, over the face cells of every tile (one thread each): FLATTEN =
-// false unites the clusters joined by the union pairs that leave the tile
-// and marks both tile-local roots as crossing (bit 15 of their L16 entry);
+// false unites the clusters joined by the union pairs that leave the tile;
 // FLATTEN = true then points every crossing root straight at its cluster
-// root and copies the cluster's flip bit into bit 14 of the crossing root's
-// entry.  Model-independent: used by the n-vector sweeps too.
+// root and, where the cluster root's flip bit differs from the crossing
+// root's own, sets bit 14 of the crossing root's entry (a correction the
+// flip kernel applies).  Model-independent: used by the n-vector sweeps too.
 template <bool FLATTEN>
 __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ Batch B)
 {
@@ -191,7 +190,6 @@ __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ B
     if (!todo) return;
     const uint32_t stamp = (uint32_t)R.st->epoch;
     unsigned long long *P = R.P;
-    unsigned *Lw = reinterpret_cast<unsigned *>(R.L16);
     bool ok = true;
     while (todo) {
         const int bit = __ffs(todo) - 1;
@@ -208,23 +206,17 @@ __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ B
             g[e] = crossing_root(R, B, cx, cy, cz, down_bit(f, v));
         }
         if (!FLATTEN) {
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const unsigned bitm = 1u << (15 + 16 * (g[e] & 1));
-                if (!(__ldcg(Lw + (g[e] >> 1)) & bitm)) atomicOr(Lw + (g[e] >> 1), bitm);
-            }
             ok &= punite(P, g[0], g[1], stamp);
         } else {
+            unsigned *Lw = reinterpret_cast<unsigned *>(R.L16);
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int rt = pfind(P, g[e], stamp);
-                if (rt != g[e]) {
-                    const unsigned long long nv = ((unsigned long long)stamp << 32) | (uint32_t)rt;
-                    if (__ldcg(P + g[e]) != nv) __stcg(P + g[e], nv);
-                }
-                // the cluster's flip bit, kept in bit 14 of the crossing
-                // root's own entry for the flip kernel
-                if ((R.F[rt >> 4] >> (rt & 15)) & 1u) {
+                if (rt == g[e]) continue;
+                const unsigned long long nv = ((unsigned long long)stamp << 32) | (uint32_t)rt;
+                if (__ldcg(P + g[e]) != nv) __stcg(P + g[e], nv);
+                const uint32_t d = (R.F[rt >> 4] >> (rt & 15)) ^ (R.F[g[e] >> 4] >> (g[e] & 15));
+                if (d & 1u) {
                     const unsigned bitm = 1u << (14 + 16 * (g[e] & 1));
                     if (!(__ldcg(Lw + (g[e] >> 1)) & bitm)) atomicOr(Lw + (g[e] >> 1), bitm);
                 }
@@ -249,7 +241,6 @@ cudaError_t ising_prepare(const TileShape &t)
     if ((int)ising_local_smem(t) > mx || (int)resolve_smem(t) > mx) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(ising_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ising_flip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(labels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return e;
 }
 
@@ -268,8 +259,7 @@ void launch_boundary(const Batch &B, int64_t ntiles, cudaStream_t s)
 
 void launch_labels(const Batch &B, int64_t ntiles, cudaStream_t s)
 {
-    const TileShape t{B.TX, B.TY, B.TZ};
-    labels_kernel<<<(unsigned)ntiles, B.TX * B.TY * B.TZ, resolve_smem(t), s>>>(B);
+    labels_kernel<<<(unsigned)ntiles, B.TX * B.TY * B.TZ, 0, s>>>(B);
 }
 
 // Phase p of a sweep: 0 local labelling, 1 crossing unions, 2 flip.

@@ -115,8 +115,8 @@ struct TileShape {
 struct Rep {
     void *spins;       // Ising: uint16 per cell; n-vector: n planes of N values
     uint16_t *L16;     // per site: tile-local index of its tile-local root (13 bits);
-                       // on a root whose cluster crosses a tile face: bit 15 set,
-                       // bit 14 = the cluster's flip bit
+                       // on a root whose cluster crosses a tile face, bit 14 =
+                       // the cluster's flip bit XOR the root's own flip bit
     unsigned long long *P;  // crossing-cluster links: (epoch stamp << 32) | parent
     uint16_t *F;       // the sweep's flip bit of every site, one word per cell
     uint32_t *dmask;   // union pairs of face cells that cross the tile (24 bits)

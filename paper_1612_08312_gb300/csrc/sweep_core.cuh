@@ -470,28 +470,21 @@ __device__ __forceinline__ int crossing_root(const Rep &R, const Batch &B, int x
     return 16 * (rx + L * (ry + L * rz)) + (lr & 15);
 }
 
-// Shared-memory bytes of the resolve stage: the tile's L16 entries (slot
+// Shared-memory bytes of the flip stage: the tile's L16 entries (slot
 // layout) and flip words.
 __host__ __device__ constexpr size_t resolve_smem_bytes(int nt) { return (size_t)16 * nt * 2 + (size_t)nt * 2 + 16; }
 
 // Resolve every site of the calling thread's cell to the global index of
-// its cluster's root and the root's flip bit.  Stages the tile's L16 and F
-// words in shared memory; roots of clusters that stay inside the tile are
-// final, the others are looked up in P (flattened: one or two hops).
-// stamp: the links' sweep stamp.  Called by every thread of the block.
-__device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, int *smem, uint32_t stamp, int root[16],
+// its cluster's root and the root's flip bit.  The tile-local root of each
+// site comes from L16; a tile-local root that was linked in P this sweep
+// (stamp) belongs to a crossing cluster and is followed to the cluster root
+// (flattened: one hop).  Called by every thread of the block.
+__device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, uint32_t stamp, int root[16],
                                              uint32_t &flip)
 {
-    const int nt = c.nt;
-    uint16_t *ls = reinterpret_cast<uint16_t *>(smem);
-    uint16_t *fs = ls + 16 * nt;
     const uint4 *src = reinterpret_cast<const uint4 *>(R.L16 + 16 * c.cell);
     const uint4 a0 = src[0], a1 = src[1];
     const uint32_t w[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-#pragma unroll
-    for (int s = 0; s < 16; ++s) ls[lslot(16 * c.t + s, nt)] = (uint16_t)(w[s >> 1] >> (16 * (s & 1)));
-    fs[c.t] = R.F[c.cell];
-    __syncthreads();
     flip = 0;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
@@ -500,25 +493,18 @@ __device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, int
         const int rx = c.ox + (lc & (c.TX - 1));
         const int ry = c.oy + ((lc >> c.lTX) & (c.TY - 1));
         const int rz = c.oz + (lc >> (c.lTX + c.lTY));
-        int g = 16 * (rx + c.L * (ry + c.L * rz)) + (lr & 15);
-        uint32_t fb;
-        if (ls[lslot(lr, nt)] & 0x8000u) {
-            g = proot(R.P, g, stamp);
-            fb = (R.F[g >> 4] >> (g & 15)) & 1u;
-        } else {
-            fb = (fs[lc] >> (lr & 15)) & 1u;
-        }
+        const int g = proot(R.P, 16 * (rx + c.L * (ry + c.L * rz)) + (lr & 15), stamp);
         root[s] = g;
-        flip |= fb << s;
+        flip |= ((R.F[g >> 4] >> (g & 15)) & 1u) << s;
     }
 }
 
 // Flip mask of the calling thread's cell (bit s = site 16 c + s flips).
-// Stages the tile's L16 and F words in shared memory.  A site's cluster
-// either stays inside the tile (its flip bit is the tile-local root's bit
-// of F) or crosses a face (its tile-local root's entry carries the cluster's
-// flip bit in bit 14, written by the crossing flatten pass).  No global
-// lookups.  Called by every thread of the block.
+// Stages the tile's L16 and F words in shared memory.  A site flips with
+// its tile-local root's bit of F, corrected by bit 14 of that root's entry
+// when its cluster crosses a tile face and the cluster root's flip bit
+// differs (written by the crossing flatten pass).  No global lookups.
+// Called by every thread of the block.
 __device__ __forceinline__ uint32_t cell_flip_mask(const TileCtx &c, const Rep &R, int *smem)
 {
     const int nt = c.nt;
@@ -535,9 +521,8 @@ __device__ __forceinline__ uint32_t cell_flip_mask(const TileCtx &c, const Rep &
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
         const int lr = (int)((w[s >> 1] >> (16 * (s & 1))) & 0x1FFFu);
-        const uint32_t re = ls[lslot(lr, nt)];
-        const uint32_t fb = (re & 0x8000u) ? ((re >> 14) & 1u) : ((fs[lr >> 4] >> (lr & 15)) & 1u);
-        flip |= fb << s;
+        const uint32_t fb = (ls[lslot(lr, nt)] >> 14) ^ (fs[lr >> 4] >> (lr & 15));
+        flip |= (fb & 1u) << s;
     }
     return flip;
 }
