@@ -174,27 +174,55 @@ __global__ void __launch_bounds__(CELL_BLOCK) ising_init_kernel(const __grid_con
 template <bool FLATTEN>
 __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ Batch B)
 {
+    // the block's crossing pairs, compacted so that every thread takes an
+    // equal share: entry (face cell << 5) | (6 f + k)
+    extern __shared__ uint16_t blist[];
+    __shared__ int bcount;
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
     const int nface = face_cells(B.TX, B.TY, B.TZ);
-    if ((int)threadIdx.x >= nface) return;
-    int lx, ly, lz;
-    face_cell_coords(B, threadIdx.x, lx, ly, lz);
     const int64_t tile = blockIdx.x - B.tile_begin[r];
     const int64_t txy = tile / R.ntx;
     const int L = R.L;
-    const int x = (int)(tile - txy * R.ntx) * B.TX + lx;
-    const int y = (int)(txy % R.nty) * B.TY + ly;
-    const int z = (int)(txy / R.nty) * B.TZ + lz;
-    uint32_t todo = R.dmask[(int64_t)x + (int64_t)L * ((int64_t)y + (int64_t)L * z)];
-    if (!todo) return;
-    const uint32_t stamp = (uint32_t)R.st->epoch;
-    unsigned long long *P = R.P;
-    bool ok = true;
+    const int ox = (int)(tile - txy * R.ntx) * B.TX;
+    const int oy = (int)(txy % R.nty) * B.TY;
+    const int oz = (int)(txy / R.nty) * B.TZ;
+    if (threadIdx.x == 0) bcount = 0;
+    __syncthreads();
+    uint32_t todo = 0;
+    if ((int)threadIdx.x < nface) {
+        int lx, ly, lz;
+        face_cell_coords(B, threadIdx.x, lx, ly, lz);
+        todo = R.dmask[(int64_t)(ox + lx) + (int64_t)L * ((int64_t)(oy + ly) + (int64_t)L * (oz + lz))];
+    }
+    const int lane = threadIdx.x & 31;
+    const int n = __popc(todo);
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
+    int base = 0;
+    if (lane == 31 && wtotal) base = atomicAdd(&bcount, wtotal);
+    int pos = __shfl_sync(0xffffffffu, base, 31) + incl - n;
     while (todo) {
         const int bit = __ffs(todo) - 1;
         todo &= todo - 1;
-        const int f = bit / 6, k = bit % 6;
+        blist[pos++] = (uint16_t)((threadIdx.x << 5) | bit);
+    }
+    __syncthreads();
+    const int np = bcount;
+    const uint32_t stamp = (uint32_t)R.st->epoch;
+    unsigned long long *P = R.P;
+    bool ok = true;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const uint32_t en = blist[i];
+        int lx, ly, lz;
+        face_cell_coords(B, (int)(en >> 5), lx, ly, lz);
+        const int x = ox + lx, y = oy + ly, z = oz + lz;
+        const int f = (int)(en & 31u) / 6, k = (int)(en & 31u) % 6;
         int g[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
@@ -253,8 +281,9 @@ void launch_boundary(const Batch &B, int64_t ntiles, cudaStream_t s)
 {
     const int nf = face_cells(B.TX, B.TY, B.TZ);
     const int threads = (nf + 31) & ~31;
-    boundary_kernel<false><<<(unsigned)ntiles, threads, 0, s>>>(B);
-    boundary_kernel<true><<<(unsigned)ntiles, threads, 0, s>>>(B);
+    const size_t smem = (size_t)nf * 24 * sizeof(uint16_t);
+    boundary_kernel<false><<<(unsigned)ntiles, threads, smem, s>>>(B);
+    boundary_kernel<true><<<(unsigned)ntiles, threads, smem, s>>>(B);
 }
 
 void launch_labels(const Batch &B, int64_t ntiles, cudaStream_t s)
