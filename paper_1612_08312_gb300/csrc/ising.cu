@@ -53,17 +53,21 @@ __global__ void __launch_bounds__(512) ising_local_kernel(const __grid_constant_
     antiparallel_groups(w[0], down_word(w), anti[0], anti[1], anti[2]);
     uint32_t act[3];
     const ByteCompare bc(R.thr);
+    if (bc.all || bc.none) {
 #pragma unroll
-    for (int g = 0; g < 3; ++g) {
-        const uint32_t sat = ~anti[g] & 0xFFFFu;
-        uint32_t a = 0;
-        if (bc.all) {
-            a = sat;
-        } else if (!bc.none && sat) {
-            // bond 48 c + 16 g + 4 f + q: byte 4 f + q of BOND call 3 c + g
-            const uint4 wd = philox_call(seed, sweep, TAG_BOND, 3 * (uint64_t)c.cell + g);
-            const uint32_t ww[4] = {wd.x, wd.y, wd.z, wd.w};
-            const uint32_t t4 = bc.t8 * 0x01010101u;
+        for (int g = 0; g < 3; ++g) act[g] = bc.all ? ~anti[g] & 0xFFFFu : 0u;
+    } else {
+        // bond 48 c + 16 g + 4 f + q: byte 4 f + q of BOND call 3 c + g; the
+        // three calls are drawn together (independent chains interleave)
+        uint4 wd[3];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) wd[g] = philox_call(seed, sweep, TAG_BOND, 3 * (uint64_t)c.cell + g);
+        const uint32_t t4 = bc.t8 * 0x01010101u;
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const uint32_t sat = ~anti[g] & 0xFFFFu;
+            const uint32_t ww[4] = {wd[g].x, wd[g].y, wd[g].z, wd[g].w};
+            uint32_t a = 0;
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
                 uint32_t nib = byte_flags_to_nibble(bytes_lt(ww[f], t4));
@@ -75,9 +79,8 @@ __global__ void __launch_bounds__(512) ising_local_kernel(const __grid_constant_
                 }
                 a |= nib << (4 * f);
             }
-            a &= sat;
+            act[g] = a & sat;
         }
-        act[g] = a;
     }
     local_core(c, R, s, act[0], act[1], act[2], sweep);
 }

@@ -243,9 +243,14 @@ __device__ __forceinline__ uint32_t cell_flip_bits(const TileCtx &c, uint64_t se
 
 // --------------------------------------------------- tile-local labelling --
 // Shared memory of the local kernels: labels (16 nt ints), union pairs
-// (12 nt words), three pair counters, tetrahedron table (64 x 16 bits); the
-// model's staging area follows.
-__host__ __device__ constexpr size_t core_smem_bytes(int nt) { return (size_t)28 * nt * 4 + 16 + 128; }
+// (15 nt words), three pair counters and a pad word, tetrahedron table (64
+// words); the model's staging area follows at the next 16-byte boundary
+// (it holds doubles and 16-byte vectors).
+__host__ __device__ constexpr int core_words(int nt) { return (31 * nt + 4 + 64 + 3) & ~3; }
+__host__ __device__ constexpr size_t core_smem_bytes(int nt) { return (size_t)core_words(nt) * 4; }
+static_assert(core_smem_bytes(1) % 16 == 0 && core_smem_bytes(2) % 16 == 0 && core_smem_bytes(8) % 16 == 0 &&
+                  core_smem_bytes(512) % 16 == 0 && core_words(1) >= 31 + 68 && core_words(2) >= 62 + 68,
+              "staging area must start on a 16-byte boundary after the core area");
 
 // Union round of the down-tetrahedron pair k of FCC point f: the pair's two
 // cells differ along the axes of m = mask(a) ^ mask(b).  Round 0: same cell
@@ -257,6 +262,21 @@ __host__ __device__ constexpr int pair_round(int f, int k)
     return ((down_mask(f, pair_a(k)) ^ down_mask(f, pair_b(k))) & 4) ? 2
          : ((down_mask(f, pair_a(k)) ^ down_mask(f, pair_b(k))) & 2) ? 1 : 0;
 }
+
+// Pairs k of the down tetrahedron of f with a vertex whose cell is a
+// backward step along axis d (bit k).
+__host__ __device__ constexpr uint32_t pair_axis_mask(int f, int d)
+{
+    uint32_t m = 0;
+    for (int k = 0; k < 6; ++k)
+        if (((down_mask(f, pair_a(k)) | down_mask(f, pair_b(k))) >> d) & 1) m |= 1u << k;
+    return m;
+}
+
+// Region of round r's pairs in the pair list: a cell has at most 7, 4 and
+// 4 spanning pairs of rounds 0, 1 and 2 (at most 3 per tetrahedron, split
+// over the rounds by the pair geometry).
+__host__ __device__ constexpr int round_base(int r, int nt) { return r == 0 ? 0 : (r == 1 ? 7 * nt : 11 * nt); }
 
 __host__ __device__ constexpr uint32_t round_mask(int r)
 {
@@ -271,7 +291,11 @@ struct CoreSmem {
     int *lab;
     uint32_t *plist;
     int *pcount;
-    uint16_t *lut;   // tetrahedron table: 8 bits of smallest vertices, 4 bits of representatives
+    // tetrahedron table, by bond pattern: bits 0-7 the smallest vertex
+    // connected to each vertex (2 bits each), bits 8-11 the component
+    // representatives, bits 16-21 the spanning pairs (pair index k of
+    // (smallest vertex, v) for every non-representative v)
+    uint32_t *lut;
     unsigned char *stage;  // model staging area (16-byte aligned)
 };
 
@@ -280,9 +304,9 @@ __device__ __forceinline__ CoreSmem core_smem(int *smem, int nt)
     CoreSmem s;
     s.lab = smem;
     s.plist = reinterpret_cast<uint32_t *>(smem + 16 * nt);
-    s.pcount = smem + 28 * nt;  // three counters
-    s.lut = reinterpret_cast<uint16_t *>(smem + 28 * nt + 4);
-    s.stage = reinterpret_cast<unsigned char *>(smem + 28 * nt + 4 + 32);
+    s.pcount = smem + 31 * nt;  // three counters
+    s.lut = reinterpret_cast<uint32_t *>(smem + 31 * nt + 4);
+    s.stage = reinterpret_cast<unsigned char *>(smem + core_words(nt));
     return s;
 }
 
@@ -297,10 +321,13 @@ __device__ __forceinline__ void core_prologue(const CoreSmem &s)
     }
     for (int i = threadIdx.x; i < 64; i += blockDim.x) {
         const uint32_t e = tet_table_entry((uint32_t)i);
-        uint32_t reps = 0;
-        for (int v = 0; v < 4; ++v)
-            if (((e >> (2 * v)) & 3u) == (uint32_t)v) reps |= 1u << v;
-        s.lut[i] = (uint16_t)(e | (reps << 8));
+        uint32_t reps = 1, span = 0;
+        for (int v = 1; v < 4; ++v) {
+            const int rv = (int)((e >> (2 * v)) & 3u);
+            if (rv == v) reps |= 1u << v;
+            else span |= 1u << pair_index(rv, v);
+        }
+        s.lut[i] = e | (reps << 8) | (span << 16);
     }
 }
 
@@ -324,30 +351,24 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
         for (int v = 0; v < 4; ++v)
             s.lab[lslot(16 * c.t + 4 * f + v, nt)] = 16 * c.t + 4 * f + (int)((uptab[f] >> (2 * v)) & 3u);
     }
+    // the down tetrahedra's spanning pairs, split into those inside the
+    // tile and those with a vertex across a backward tile face
     uint32_t inpairs = 0, cross = 0;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        const uint32_t dt = s.lut[down_tet_index(C, Bg, f)];
-#pragma unroll
-        for (int v = 1; v < 4; ++v) {
-            const int rv = (int)((dt >> (2 * v)) & 3u);
-            if (rv == v) continue;
-            const int k = pair_index(rv, v);
-            bool inside = !(down_mask(f, v) & out);
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-                if (rv == u) inside = inside && !(down_mask(f, u) & out);
-            if (inside) inpairs |= 1u << (6 * f + k);
-            else cross |= 1u << (6 * f + k);
-        }
+        const uint32_t span = (s.lut[down_tet_index(C, Bg, f)] >> 16) & 0x3Fu;
+        const uint32_t leave = ((out & 1u) ? pair_axis_mask(f, 0) : 0u) | ((out & 2u) ? pair_axis_mask(f, 1) : 0u) |
+                               ((out & 4u) ? pair_axis_mask(f, 2) : 0u);
+        inpairs |= (span & ~leave) << (6 * f);
+        cross |= (span & leave) << (6 * f);
     }
-    bool ok = true;
+    // every round's pairs go to the round's own region of the pair list
+    // before the first union
 #pragma unroll
     for (int rnd = 0; rnd < 3; ++rnd) {
-        __syncthreads();  // labels initialised / previous round flattened
         const uint32_t mine = inpairs & round_mask(rnd);
         const int n = __popc(mine);
-        int base = n ? atomicAdd(s.pcount + rnd, n) : 0;
+        int base = round_base(rnd, nt) + (n ? atomicAdd(s.pcount + rnd, n) : 0);
 #pragma unroll
         for (int f = 0; f < 4; ++f)
 #pragma unroll
@@ -358,13 +379,18 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
                     const int b = 16 * vertex_local_cell(c, down_mask(f, vb)) + down_bit(f, vb);
                     s.plist[base++] = (uint32_t)a | ((uint32_t)b << 16);
                 }
-        __syncthreads();
+    }
+    bool ok = true;
+#pragma unroll
+    for (int rnd = 0; rnd < 3; ++rnd) {
+        __syncthreads();  // labels initialised and pairs listed / previous round flattened
         const int np = s.pcount[rnd];
+        const uint32_t *pl = s.plist + round_base(rnd, nt);
         for (int e = threadIdx.x; e < np; e += nt) {
-            const uint32_t pr = s.plist[e];
+            const uint32_t pr = pl[e];
             ok &= sunite(s.lab, (int)(pr & 0xFFFFu), (int)(pr >> 16), nt);
         }
-        __syncthreads();
+        __syncthreads();  // the round's unions done
         // point this cell's component representatives straight at their roots
 #pragma unroll
         for (int sb = 0; sb < 16; ++sb)
