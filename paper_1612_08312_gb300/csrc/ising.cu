@@ -4,8 +4,8 @@
 // 16 c + s; 1 means s = -1).  Every kernel runs over a Batch of one or more
 // lattices, one CTA per tile of TX x TY x TZ cells, one thread per cell.
 //
-//   ising_local     stages the tile's spin words plus a one-cell halo on the
-//                   backward faces, forms the 48 bonds' antiparallel bits by
+//   ising_local     reads its cell's spin word and those of the backward
+//                   neighbour cells, forms the 48 bonds' antiparallel bits by
 //                   shift-XOR, draws one Philox call per 16 bonds and
 //                   compares its bytes with the threshold four at a time
 //                   (a satisfied bond is active with p = 1 - exp(-2 beta J),
@@ -20,19 +20,6 @@
 
 namespace pyro {
 
-// Stage the tile's spin words and its backward halo into hs.
-__device__ __forceinline__ void stage_spin_halo(const TileCtx &c, const uint16_t *spins, uint16_t *hs)
-{
-    const int nh = halo_cells(c.TX, c.TY, c.TZ);
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) hs[h] = spins[halo_cell(h, c.TX, c.TY, c.ox, c.oy, c.oz, c.L)];
-}
-
-__device__ __forceinline__ void cell_words(const TileCtx &c, const uint16_t *hs, uint32_t w[7])
-{
-#pragma unroll
-    for (int m = 0; m < 7; ++m) w[m] = hs[halo_index(c, m)];
-}
-
 __global__ void __launch_bounds__(512) ising_local_kernel(const __grid_constant__ Batch B)
 {
     extern __shared__ __align__(16) int smem[];
@@ -40,15 +27,24 @@ __global__ void __launch_bounds__(512) ising_local_kernel(const __grid_constant_
     const Rep &R = B.reps[r];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
     const CoreSmem s = core_smem(smem, c.nt);
-    uint16_t *hs = reinterpret_cast<uint16_t *>(s.stage);
     const uint32_t sweep = (uint32_t)R.st->sweep;
     const uint64_t seed = R.seed;
     core_prologue(s);
-    stage_spin_halo(c, static_cast<const uint16_t *>(R.spins), hs);
-    __syncthreads();
-
+    // the cell's spin word and those of the cells one step back along the
+    // axes of each mask m (read straight from global memory, L1-cached)
+    const uint16_t *spins = static_cast<const uint16_t *>(R.spins);
     uint32_t w[7];
-    cell_words(c, hs, w);
+    {
+        const int L = c.L;
+        const int x = c.ox + c.lx, y = c.oy + c.ly, z = c.oz + c.lz;
+        const int xm = wrap_back(x, L), ym = wrap_back(y, L), zm = wrap_back(z, L);
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+            const int cx = (m & 1) ? xm : x, cy = (m & 2) ? ym : y, cz = (m & 4) ? zm : z;
+            w[m] = spins[(uint32_t)cx + (uint32_t)L * ((uint32_t)cy + (uint32_t)L * (uint32_t)cz)];
+        }
+    }
+    __syncthreads();  // table and pair counters ready
     uint32_t anti[3];
     antiparallel_groups(w[0], down_word(w), anti[0], anti[1], anti[2]);
     uint32_t act[3];
@@ -184,12 +180,12 @@ __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ B
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
     const int nface = face_cells(B.TX, B.TY, B.TZ);
-    const int64_t tile = blockIdx.x - B.tile_begin[r];
-    const int64_t txy = tile / R.ntx;
+    const uint32_t tile = (uint32_t)(blockIdx.x - B.tile_begin[r]);
+    const uint32_t txy = tile / (uint32_t)R.ntx;
     const int L = R.L;
-    const int ox = (int)(tile - txy * R.ntx) * B.TX;
-    const int oy = (int)(txy % R.nty) * B.TY;
-    const int oz = (int)(txy / R.nty) * B.TZ;
+    const int ox = (int)(tile - txy * (uint32_t)R.ntx) * B.TX;
+    const int oy = (int)(txy % (uint32_t)R.nty) * B.TY;
+    const int oz = (int)(txy / (uint32_t)R.nty) * B.TZ;
     if (threadIdx.x == 0) bcount = 0;
     __syncthreads();
     uint32_t todo = 0;
@@ -260,9 +256,7 @@ __global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ B
 // ------------------------------------------------------------ launchers --
 cudaError_t ising_set_unite_bound(int bound) { return cudaMemcpyToSymbol(c_unite_bound, &bound, sizeof(int)); }
 
-static size_t halo_spin_bytes(const TileShape &t) { return (size_t)halo_cells(t.TX, t.TY, t.TZ) * sizeof(uint16_t); }
-
-size_t ising_local_smem(const TileShape &t) { return core_smem_bytes(t.TX * t.TY * t.TZ) + halo_spin_bytes(t); }
+size_t ising_local_smem(const TileShape &t) { return core_smem_bytes(t.TX * t.TY * t.TZ); }
 
 size_t resolve_smem(const TileShape &t) { return resolve_smem_bytes(t.TX * t.TY * t.TZ); }
 

@@ -42,10 +42,12 @@ __device__ __forceinline__ TileCtx tile_ctx(const Batch &B, const Rep &R, int64_
     c.lTY = B.lTY;
     c.nt = B.TX * B.TY * B.TZ;
     c.L = R.L;
-    const int64_t txy = tile / R.ntx;
-    c.ox = (int)(tile - txy * R.ntx) * c.TX;
-    c.oy = (int)(txy % R.nty) * c.TY;
-    c.oz = (int)(txy / R.nty) * c.TZ;
+    // a lattice has fewer than 2^31 tiles (L <= 511): 32-bit divisions
+    const uint32_t tl = (uint32_t)tile, ntx = (uint32_t)R.ntx, nty = (uint32_t)R.nty;
+    const uint32_t txy = tl / ntx;
+    c.ox = (int)(tl - txy * ntx) * c.TX;
+    c.oy = (int)(txy % nty) * c.TY;
+    c.oz = (int)(txy / nty) * c.TZ;
     c.t = threadIdx.x;
     c.lx = c.t & (c.TX - 1);
     c.ly = (c.t >> c.lTX) & (c.TY - 1);
