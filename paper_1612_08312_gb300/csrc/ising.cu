@@ -170,8 +170,10 @@ __global__ void __launch_bounds__(CELL_BLOCK) ising_init_kernel(const __grid_con
 // root and, where the cluster root's flip bit differs from the crossing
 // root's own, sets bit 14 of the crossing root's entry (a correction the
 // flip kernel applies).  Model-independent: used by the n-vector sweeps too.
+// Latency-bound chains of scattered loads: at most 32 registers, so that
+// ten blocks of a 8 x 8 x 8 tile's 192 threads fit on an SM.
 template <bool FLATTEN>
-__global__ void __launch_bounds__(512) boundary_kernel(const __grid_constant__ Batch B)
+__global__ void __launch_bounds__(512, 4) boundary_kernel(const __grid_constant__ Batch B)
 {
     // the block's crossing pairs, compacted so that every thread takes an
     // equal share: entry (face cell << 5) | (6 f + k)

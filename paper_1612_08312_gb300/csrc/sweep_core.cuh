@@ -280,6 +280,11 @@ __host__ __device__ constexpr uint32_t pair_axis_mask(int f, int d)
 // over the rounds by the pair geometry).
 __host__ __device__ constexpr int round_base(int r, int nt) { return r == 0 ? 0 : (r == 1 ? 7 * nt : 11 * nt); }
 
+// Bit 6 f + k of the pair (0, f) of the down tetrahedron of f = 1..3 (pair
+// index k = f - 1): its two vertices lie in the owning cell itself.
+__host__ __device__ constexpr int own_pair_bit(int f) { return 7 * f - 1; }
+__host__ __device__ constexpr uint32_t own_pair_bits() { return (1u << 6) | (1u << 13) | (1u << 20); }
+
 __host__ __device__ constexpr uint32_t round_mask(int r)
 {
     uint32_t m = 0;
@@ -343,16 +348,6 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
 {
     const int nt = c.nt;
     const uint32_t out = (c.bx ? 1u : 0u) | (c.by ? 2u : 0u) | (c.bz ? 4u : 0u);  // axes whose backward step leaves
-    uint32_t uptab[4];
-    uint32_t reps = 0;  // bit 4 f + v: site is its up-tetrahedron component's representative
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        uptab[f] = s.lut[up_tet_index(A, Bg, f)];
-        reps |= ((uptab[f] >> 8) & 0xFu) << (4 * f);
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-            s.lab[lslot(16 * c.t + 4 * f + v, nt)] = 16 * c.t + 4 * f + (int)((uptab[f] >> (2 * v)) & 3u);
-    }
     // the down tetrahedra's spanning pairs, split into those inside the
     // tile and those with a vertex across a backward tile face
     uint32_t inpairs = 0, cross = 0;
@@ -363,6 +358,26 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
                                ((out & 4u) ? pair_axis_mask(f, 2) : 0u);
         inpairs |= (span & ~leave) << (6 * f);
         cross |= (span & leave) << (6 * f);
+    }
+    // The pair (0, f) of the down tetrahedron of f = 1..3 joins site 4 f
+    // (vertex 0 of up tetrahedron f) and site f (vertex f of up tetrahedron
+    // 0), both in this cell: those three unions are made here, in the
+    // initial labels, instead of in shared memory.
+    const uint32_t own = inpairs & own_pair_bits();
+    inpairs ^= own;
+    uint32_t uptab[4];
+    uint32_t reps = 0;  // bit 4 f + v: site is its component's representative
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        uptab[f] = s.lut[up_tet_index(A, Bg, f)];
+        const bool joined = f > 0 && ((own >> own_pair_bit(f)) & 1u);
+        reps |= (((uptab[f] >> 8) & 0xFu) & (joined ? ~1u : ~0u)) << (4 * f);
+        const int rep0 = (int)((uptab[0] >> (2 * f)) & 3u);  // site f's representative in up tetrahedron 0
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int rv = (int)((uptab[f] >> (2 * v)) & 3u);
+            s.lab[lslot(16 * c.t + 4 * f + v, nt)] = 16 * c.t + ((joined && rv == 0) ? rep0 : 4 * f + rv);
+        }
     }
     // every round's pairs go to the round's own region of the pair list
     // before the first union
@@ -409,8 +424,10 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
     // another thread's path halving after it was flattened, so follow it to
     // the root (no label changes any more: a read-only walk).
     uint32_t packed[8];
+    uint32_t root0[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
+        const bool joined = f > 0 && ((own >> own_pair_bit(f)) & 1u);
         uint32_t root[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -419,8 +436,12 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
 #pragma unroll
             for (int u = 0; u < v; ++u)
                 if (rv == (uint32_t)u) r = root[u];
-            if (rv == (uint32_t)v) r = (uint32_t)sroot(s.lab, 16 * c.t + 4 * f + v, nt);
+            if (rv == (uint32_t)v) r = (v == 0 && joined) ? root0[f] : (uint32_t)sroot(s.lab, 16 * c.t + 4 * f + v, nt);
             root[v] = r;
+        }
+        if (f == 0) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) root0[v] = root[v];
         }
         packed[2 * f] = root[0] | (root[1] << 16);
         packed[2 * f + 1] = root[2] | (root[3] << 16);
