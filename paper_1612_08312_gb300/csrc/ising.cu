@@ -166,10 +166,10 @@ __global__ void __launch_bounds__(CELL_BLOCK) ising_init_kernel(const __grid_con
 
 // Phase 1, over the face cells of every tile (one thread each): FLATTEN =
 // false unites the clusters joined by the union pairs that leave the tile;
-// FLATTEN = true then points every crossing root straight at its cluster
-// root and, where the cluster root's flip bit differs from the crossing
-// root's own, sets bit 14 of the crossing root's entry (a correction the
-// flip kernel applies).  Model-independent: used by the n-vector sweeps too.
+// FLATTEN = true then finds every crossing root's cluster root and, where
+// the cluster root's flip bit differs from the crossing root's own, sets
+// bit 14 of the crossing root's entry (a correction the flip kernel
+// applies).  Model-independent: used by the n-vector sweeps too.
 // Latency-bound chains of scattered loads: at most 32 registers, so that
 // ten blocks of a 8 x 8 x 8 tile's 192 threads fit on an SM.
 template <bool FLATTEN>
@@ -234,17 +234,30 @@ __global__ void __launch_bounds__(512, 4) boundary_kernel(const __grid_constant_
             const int cz = (m & 4) ? wrap_back(z, L) : z;
             g[e] = crossing_root(R, B, cx, cy, cz, down_bit(f, v));
         }
+        if (g[0] == g[1]) continue;  // both ends in one tile-local cluster
         if (!FLATTEN) {
             ok &= punite(P, g[0], g[1], stamp);
         } else {
+            // both ends' cluster roots, walked together and read-only (all
+            // unions are done; the links stay as they are); a tile-local
+            // root that is not its cluster's root gets the correction bit
+            // where the two flip bits differ
+            int rt[2] = {g[0], g[1]};
+            unsigned long long v[2] = {__ldcg(P + g[0]), __ldcg(P + g[1])};
+#pragma unroll 1
+            for (int it = 0; it < (1 << 20) && (plinked(v[0], stamp) || plinked(v[1], stamp)); ++it) {
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+                    if (plinked(v[e], stamp)) rt[e] = (int)(uint32_t)v[e];
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+                    if (plinked(v[e], stamp)) v[e] = __ldcg(P + rt[e]);
+            }
             unsigned *Lw = reinterpret_cast<unsigned *>(R.L16);
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const int rt = pfind(P, g[e], stamp);
-                if (rt == g[e]) continue;
-                const unsigned long long nv = ((unsigned long long)stamp << 32) | (uint32_t)rt;
-                if (__ldcg(P + g[e]) != nv) __stcg(P + g[e], nv);
-                const uint32_t d = (R.F[rt >> 4] >> (rt & 15)) ^ (R.F[g[e] >> 4] >> (g[e] & 15));
+                if (rt[e] == g[e]) continue;
+                const uint32_t d = (R.F[rt[e] >> 4] >> (rt[e] & 15)) ^ (R.F[g[e] >> 4] >> (g[e] & 15));
                 if (d & 1u) {
                     const unsigned bitm = 1u << (14 + 16 * (g[e] & 1));
                     if (!(__ldcg(Lw + (g[e] >> 1)) & bitm)) atomicOr(Lw + (g[e] >> 1), bitm);

@@ -459,37 +459,47 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
 // clearing: linking a root is a compare-and-swap from the value just read.
 // The larger root is always hung under the smaller one, so a cluster's root
 // stays its minimum site index.
-__device__ __forceinline__ int pfind(unsigned long long *P, int x, uint32_t stamp)
+__device__ __forceinline__ bool plinked(unsigned long long v, uint32_t stamp) { return (uint32_t)(v >> 32) == stamp; }
+
+// One find step with path splitting: x (entry v, a current link) moves to
+// its parent, whose entry is returned in v; x's entry is pointed at its
+// grandparent if that is a current link.  One dependent load per level.
+__device__ __forceinline__ void pstep(unsigned long long *P, int &x, unsigned long long &v, uint32_t stamp)
 {
-#pragma unroll 1
-    for (int it = 0; it < (1 << 20); ++it) {
-        const unsigned long long v = __ldcg(P + x);
-        if ((uint32_t)(v >> 32) != stamp) return x;
-        const int p = (int)(uint32_t)v;
-        // path halving: point x at its grandparent if that is a current link
-        const unsigned long long gv = __ldcg(P + p);
-        if ((uint32_t)(gv >> 32) == stamp) __stcg(P + x, gv);
-        x = p;
-    }
-    return x;
+    const int p = (int)(uint32_t)v;
+    const unsigned long long gv = __ldcg(P + p);
+    if (plinked(gv, stamp)) __stcg(P + x, gv);
+    x = p;
+    v = gv;
 }
 
+// Union of the crossing clusters of a and b.  Both finds walk in lockstep
+// (their loads overlap); a root is linked by a compare-and-swap from the
+// entry value its walk ended on.  Returns false if the bound was hit.
 __device__ __forceinline__ bool punite(unsigned long long *P, int a, int b, uint32_t stamp)
 {
+    unsigned long long va = __ldcg(P + a), vb = __ldcg(P + b);
 #pragma unroll 1
-    for (int it = 0; it < 65536; ++it) {
-        a = pfind(P, a, stamp);
-        b = pfind(P, b, stamp);
+    for (int it = 0; it < (1 << 20); ++it) {
+        const bool la = plinked(va, stamp), lb = plinked(vb, stamp);
+        if (la || lb) {
+            if (la) pstep(P, a, va, stamp);
+            if (lb) pstep(P, b, vb, stamp);
+            continue;
+        }
         if (a == b) return true;
         if (a > b) {
             const int t = a;
             a = b;
             b = t;
+            const unsigned long long tv = va;
+            va = vb;
+            vb = tv;
         }
-        const unsigned long long old = __ldcg(P + b);
-        if ((uint32_t)(old >> 32) == stamp) continue;  // b was linked meanwhile
         const unsigned long long nv = ((unsigned long long)stamp << 32) | (uint32_t)a;
-        if (atomicCAS(P + b, old, nv) == old) return true;
+        const unsigned long long old = atomicCAS(P + b, vb, nv);
+        if (old == vb) return true;
+        vb = old;  // b was linked meanwhile: walk on from its new entry
     }
     return false;
 }
@@ -526,8 +536,8 @@ __host__ __device__ constexpr size_t resolve_smem_bytes(int nt) { return (size_t
 // Resolve every site of the calling thread's cell to the global index of
 // its cluster's root and the root's flip bit.  The tile-local root of each
 // site comes from L16; a tile-local root that was linked in P this sweep
-// (stamp) belongs to a crossing cluster and is followed to the cluster root
-// (flattened: one hop).  Called by every thread of the block.
+// (stamp) belongs to a crossing cluster and its links are followed to the
+// cluster root.  Called by every thread of the block.
 __device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, uint32_t stamp, int root[16],
                                              uint32_t &flip)
 {
