@@ -16,9 +16,14 @@
 //                   integers; energy of Eq. 1, magnetisation of Eq. 2).
 //   boundary_kernel unites the clusters that cross tile faces (all models).
 //   labels_kernel   writes the canonical label of every site on demand.
+#include <algorithm>
+
 #include "sweep_core.cuh"
 
 namespace pyro {
+
+// Threads of a measurement block (a tile of up to 512 cells, four per thread).
+constexpr int MEASURE_BLOCK = 128;
 
 __global__ void __launch_bounds__(512) ising_local_kernel(const __grid_constant__ Batch B)
 {
@@ -108,28 +113,33 @@ __global__ void __launch_bounds__(512) labels_kernel(const __grid_constant__ Bat
 
 // Antiparallel bonds (48 per cell) and -1 spins: exact integer counts per
 // tile, written to the tile's partial slot.
-__global__ void __launch_bounds__(512) ising_measure_kernel(const __grid_constant__ Batch B)
+__global__ void __launch_bounds__(MEASURE_BLOCK) ising_measure_kernel(const __grid_constant__ Batch B)
 {
     const int r = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[r];
-    const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);
+    const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[r]);  // the tile's origin
     const uint16_t *spins = static_cast<const uint16_t *>(R.spins);
     const int L = c.L;
-    const int x = c.ox + c.lx, y = c.oy + c.ly, z = c.oz + c.lz;
-    uint32_t w[7];
+    unsigned anti = 0, ndown = 0;
+    // up to four cells per thread: their 28 spin-word loads are independent
+#pragma unroll 4
+    for (int t = threadIdx.x; t < c.nt; t += blockDim.x) {
+        const int x = c.ox + (t & (c.TX - 1)), y = c.oy + ((t >> c.lTX) & (c.TY - 1)), z = c.oz + (t >> (c.lTX + c.lTY));
+        const int xm = wrap_back(x, L), ym = wrap_back(y, L), zm = wrap_back(z, L);
+        uint32_t w[7];
 #pragma unroll
-    for (int m = 0; m < 7; ++m) {
-        const int cx = (m & 1) ? wrap_back(x, L) : x;
-        const int cy = (m & 2) ? wrap_back(y, L) : y;
-        const int cz = (m & 4) ? wrap_back(z, L) : z;
-        w[m] = spins[(int64_t)cx + (int64_t)L * ((int64_t)cy + (int64_t)L * cz)];
+        for (int m = 0; m < 7; ++m) {
+            const int cx = (m & 1) ? xm : x, cy = (m & 2) ? ym : y, cz = (m & 4) ? zm : z;
+            w[m] = spins[(uint32_t)cx + (uint32_t)L * ((uint32_t)cy + (uint32_t)L * (uint32_t)cz)];
+        }
+        uint32_t A, Bg, C;
+        antiparallel_groups(w[0], down_word(w), A, Bg, C);
+        anti += (unsigned)(__popc(A) + __popc(Bg) + __popc(C));
+        ndown += (unsigned)__popc(w[0]);
     }
-    uint32_t A, Bg, C;
-    antiparallel_groups(w[0], down_word(w), A, Bg, C);
-    const unsigned mask = lanes_mask(c.nt);
-    const unsigned anti = __reduce_add_sync(mask, (unsigned)(__popc(A) + __popc(Bg) + __popc(C)));
-    const unsigned ndown = __reduce_add_sync(mask, (unsigned)__popc(w[0]));
-    __shared__ unsigned red[2][16];
+    anti = __reduce_add_sync(0xffffffffu, anti);  // blockDim is a multiple of 32
+    ndown = __reduce_add_sync(0xffffffffu, ndown);
+    __shared__ unsigned red[2][MEASURE_BLOCK / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][wid] = anti;
@@ -138,7 +148,7 @@ __global__ void __launch_bounds__(512) ising_measure_kernel(const __grid_constan
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long sa = 0, sd = 0;
-        for (int q = 0; q < (c.nt + 31) / 32; ++q) {
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
             sa += red[0][q];
             sd += red[1][q];
         }
@@ -315,7 +325,9 @@ void ising_launch_phase(int p, const Batch &B, int64_t ntiles, cudaStream_t s)
 
 void ising_launch_measure(const Batch &B, int64_t ntiles, cudaStream_t s)
 {
-    ising_measure_kernel<<<(unsigned)ntiles, B.TX * B.TY * B.TZ, 0, s>>>(B);
+    const int nt = B.TX * B.TY * B.TZ;
+    const int threads = std::min(MEASURE_BLOCK, std::max(32, ((nt + 3) / 4 + 31) & ~31));
+    ising_measure_kernel<<<(unsigned)ntiles, threads, 0, s>>>(B);
 }
 
 }  // namespace pyro

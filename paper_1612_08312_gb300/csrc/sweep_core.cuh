@@ -529,9 +529,8 @@ __device__ __forceinline__ int crossing_root(const Rep &R, const Batch &B, int x
     return 16 * (rx + L * (ry + L * rz)) + (lr & 15);
 }
 
-// Shared-memory bytes of the flip stage: the tile's L16 entries (slot
-// layout) and flip words.
-__host__ __device__ constexpr size_t resolve_smem_bytes(int nt) { return (size_t)16 * nt * 2 + (size_t)nt * 2 + 16; }
+// Shared-memory bytes of the flip stage: one corrected flip word per cell.
+__host__ __device__ constexpr size_t resolve_smem_bytes(int nt) { return (size_t)nt * 2 + 16; }
 
 // Resolve every site of the calling thread's cell to the global index of
 // its cluster's root and the root's flip bit.  The tile-local root of each
@@ -558,30 +557,29 @@ __device__ __forceinline__ void resolve_cell(const TileCtx &c, const Rep &R, uin
     }
 }
 
-// Flip mask of the calling thread's cell (bit s = site 16 c + s flips).
-// Stages the tile's L16 and F words in shared memory.  A site flips with
-// its tile-local root's bit of F, corrected by bit 14 of that root's entry
-// when its cluster crosses a tile face and the cluster root's flip bit
-// differs (written by the crossing flatten pass).  No global lookups.
+// Flip mask of the calling thread's cell (bit s = site 16 c + s flips).  A
+// site flips with its tile-local root's bit of F, corrected by bit 14 of
+// that root's L16 entry when its cluster crosses a tile face and the
+// cluster root's flip bit differs (written by the crossing pass).  Each
+// thread folds its own cell's correction bits into its F word, so the tile
+// shares one 16-bit word per cell in shared memory.  No global lookups.
 // Called by every thread of the block.
 __device__ __forceinline__ uint32_t cell_flip_mask(const TileCtx &c, const Rep &R, int *smem)
 {
-    const int nt = c.nt;
-    uint16_t *ls = reinterpret_cast<uint16_t *>(smem);
-    uint16_t *fs = ls + 16 * nt;
+    uint16_t *fx = reinterpret_cast<uint16_t *>(smem);
     const uint4 *src = reinterpret_cast<const uint4 *>(R.L16 + 16 * c.cell);
     const uint4 a0 = src[0], a1 = src[1];
     const uint32_t w[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    uint32_t corr = 0;
 #pragma unroll
-    for (int s = 0; s < 16; ++s) ls[lslot(16 * c.t + s, nt)] = (uint16_t)(w[s >> 1] >> (16 * (s & 1)));
-    fs[c.t] = R.F[c.cell];
+    for (int i = 0; i < 8; ++i) corr |= (((w[i] >> 14) & 1u) | ((w[i] >> 29) & 2u)) << (2 * i);
+    fx[c.t] = (uint16_t)(R.F[c.cell] ^ corr);
     __syncthreads();
     uint32_t flip = 0;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
         const int lr = (int)((w[s >> 1] >> (16 * (s & 1))) & 0x1FFFu);
-        const uint32_t fb = (ls[lslot(lr, nt)] >> 14) ^ (fs[lr >> 4] >> (lr & 15));
-        flip |= (fb & 1u) << s;
+        flip |= ((fx[lr >> 4] >> (lr & 15)) & 1u) << s;
     }
     return flip;
 }
