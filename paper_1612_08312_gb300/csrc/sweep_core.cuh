@@ -256,9 +256,10 @@ static_assert(core_smem_bytes(1) % 16 == 0 && core_smem_bytes(2) % 16 == 0 && co
 
 // Union round of the down-tetrahedron pair k of FCC point f: the pair's two
 // cells differ along the axes of m = mask(a) ^ mask(b).  Round 0: same cell
-// or x only; round 1: y without z; round 2: z.  After each round every
-// component representative is pointed straight at its root, so the finds
-// of the next round start from depth one.
+// or x only; round 1: y without z; round 2: z.  The rounds are separated by
+// block barriers, so the trees grow row by row, then plane by plane; after
+// the last round every component representative is pointed straight at
+// its root.
 __host__ __device__ constexpr int pair_round(int f, int k)
 {
     return ((down_mask(f, pair_a(k)) ^ down_mask(f, pair_b(k))) & 4) ? 2
@@ -400,23 +401,23 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
     bool ok = true;
 #pragma unroll
     for (int rnd = 0; rnd < 3; ++rnd) {
-        __syncthreads();  // labels initialised and pairs listed / previous round flattened
+        __syncthreads();  // labels initialised and pairs listed / previous round's unions done
         const int np = s.pcount[rnd];
         const uint32_t *pl = s.plist + round_base(rnd, nt);
         for (int e = threadIdx.x; e < np; e += nt) {
             const uint32_t pr = pl[e];
             ok &= sunite(s.lab, (int)(pr & 0xFFFFu), (int)(pr >> 16), nt);
         }
-        __syncthreads();  // the round's unions done
-        // point this cell's component representatives straight at their roots
-#pragma unroll
-        for (int sb = 0; sb < 16; ++sb)
-            if ((reps >> sb) & 1u) {
-                const int x = 16 * c.t + sb;
-                const int r = sfind(s.lab, x, nt);
-                s.lab[lslot(x, nt)] = r;
-            }
     }
+    __syncthreads();  // all unions done
+    // point this cell's component representatives straight at their roots
+#pragma unroll
+    for (int sb = 0; sb < 16; ++sb)
+        if ((reps >> sb) & 1u) {
+            const int x = 16 * c.t + sb;
+            const int r = sfind(s.lab, x, nt);
+            s.lab[lslot(x, nt)] = r;
+        }
     if (!ok) atomicOr(&R.st->status, ST_NOCONVERGE);
     __syncthreads();
     // every site takes the root of its up-tetrahedron representative.  A
