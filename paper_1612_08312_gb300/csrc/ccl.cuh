@@ -49,16 +49,31 @@ __device__ __forceinline__ int sroot(const volatile int *lab, int x, int nt)
 // pyro_debug_set to exercise the bound-exceeded status path.
 static __constant__ int c_unite_bound = 4096;
 
-// Union of the clusters of a and b in shared memory.  Returns false if the
-// iteration bound was hit.
+// Union of the clusters of a and b in shared memory.  Both finds walk in
+// lockstep (path splitting), so their shared-memory loads overlap.
+// Returns false if the iteration bound was hit.
 __device__ __forceinline__ bool sunite(int *lab, int a, int b, int nt)
 {
     volatile int *vl = lab;
     const int bound = c_unite_bound;
+    int pa = vl[lslot(a, nt)], pb = vl[lslot(b, nt)];
 #pragma unroll 1
     for (int it = 0; it < bound; ++it) {
-        a = sfind(vl, a, nt);
-        b = sfind(vl, b, nt);
+#pragma unroll 1
+        for (int st = 0; (pa != a || pb != b) && st < 65536; ++st) {
+            if (pa != a) {
+                const int g = vl[lslot(pa, nt)];
+                if (g != pa) vl[lslot(a, nt)] = g;
+                a = pa;
+                pa = g;
+            }
+            if (pb != b) {
+                const int g = vl[lslot(pb, nt)];
+                if (g != pb) vl[lslot(b, nt)] = g;
+                b = pb;
+                pb = g;
+            }
+        }
         if (a == b) return true;
         if (a > b) {
             const int t = a;
@@ -67,7 +82,10 @@ __device__ __forceinline__ bool sunite(int *lab, int a, int b, int nt)
         }
         const int old = atomicMin(&lab[lslot(b, nt)], a);
         if (old == b) return true;
-        b = old;  // b had been linked meanwhile: unite a with its new parent
+        // b had been linked meanwhile: unite a with its new parent
+        b = old;
+        pa = vl[lslot(a, nt)];
+        pb = vl[lslot(b, nt)];
     }
     return false;
 }
