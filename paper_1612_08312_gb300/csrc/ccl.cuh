@@ -33,18 +33,6 @@ __device__ __forceinline__ int sfind(volatile int *lab, int x, int nt)
     return x;
 }
 
-// Root of x when no thread writes labels any more (read-only walk).
-__device__ __forceinline__ int sroot(const volatile int *lab, int x, int nt)
-{
-    int p = lab[lslot(x, nt)];
-#pragma unroll 1
-    for (int it = 0; p != x && it < 65536; ++it) {
-        x = p;
-        p = lab[lslot(x, nt)];
-    }
-    return x;
-}
-
 // Iteration bound of one union (4096).  A test can lower it (to 0) through
 // pyro_debug_set to exercise the bound-exceeded status path.
 static __constant__ int c_unite_bound = 4096;

@@ -410,20 +410,11 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
         }
     }
     __syncthreads();  // all unions done
-    // point this cell's component representatives straight at their roots
-#pragma unroll
-    for (int sb = 0; sb < 16; ++sb)
-        if ((reps >> sb) & 1u) {
-            const int x = 16 * c.t + sb;
-            const int r = sfind(s.lab, x, nt);
-            s.lab[lslot(x, nt)] = r;
-        }
     if (!ok) atomicOr(&R.st->status, ST_NOCONVERGE);
-    __syncthreads();
-    // every site takes the root of its up-tetrahedron representative.  A
-    // representative's entry may have been reset to an older ancestor by
-    // another thread's path halving after it was flattened, so follow it to
-    // the root (no label changes any more: a read-only walk).
+    // every site takes the root of its component's representative.  The
+    // representatives are this thread's own sites: each one's root is found
+    // (no unions any more, so the walk ends at the true root) and stored in
+    // its entry, which shortens the other threads' walks through it.
     uint32_t packed[8];
     uint32_t root0[4];
 #pragma unroll
@@ -437,7 +428,15 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
 #pragma unroll
             for (int u = 0; u < v; ++u)
                 if (rv == (uint32_t)u) r = root[u];
-            if (rv == (uint32_t)v) r = (v == 0 && joined) ? root0[f] : (uint32_t)sroot(s.lab, 16 * c.t + 4 * f + v, nt);
+            if (rv == (uint32_t)v) {
+                if (v == 0 && joined) {
+                    r = root0[f];
+                } else {
+                    const int x = 16 * c.t + 4 * f + v;
+                    r = (uint32_t)sfind(s.lab, x, nt);
+                    s.lab[lslot(x, nt)] = (int)r;
+                }
+            }
             root[v] = r;
         }
         if (f == 0) {
