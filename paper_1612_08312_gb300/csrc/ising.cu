@@ -249,11 +249,13 @@ __global__ void __launch_bounds__(512, 4) boundary_kernel(const __grid_constant_
             ok &= punite(P, g[0], g[1], stamp);
         } else {
             // both ends' cluster roots, walked together and read-only (all
-            // unions are done; the links stay as they are); a tile-local
-            // root that is not its cluster's root gets the correction bit
-            // where the two flip bits differ
+            // unions are done and this pass writes no link, so the loads
+            // may take the cached read-only path: many crossing roots share
+            // one cluster root); a tile-local root that is not its
+            // cluster's root gets the correction bit where the two flip
+            // bits differ
             int rt[2] = {g[0], g[1]};
-            unsigned long long v[2] = {__ldcg(P + g[0]), __ldcg(P + g[1])};
+            unsigned long long v[2] = {__ldg(P + g[0]), __ldg(P + g[1])};
 #pragma unroll 1
             for (int it = 0; it < (1 << 20) && (plinked(v[0], stamp) || plinked(v[1], stamp)); ++it) {
 #pragma unroll
@@ -261,13 +263,13 @@ __global__ void __launch_bounds__(512, 4) boundary_kernel(const __grid_constant_
                     if (plinked(v[e], stamp)) rt[e] = (int)(uint32_t)v[e];
 #pragma unroll
                 for (int e = 0; e < 2; ++e)
-                    if (plinked(v[e], stamp)) v[e] = __ldcg(P + rt[e]);
+                    if (plinked(v[e], stamp)) v[e] = __ldg(P + rt[e]);
             }
             unsigned *Lw = reinterpret_cast<unsigned *>(R.L16);
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 if (rt[e] == g[e]) continue;
-                const uint32_t d = (R.F[rt[e] >> 4] >> (rt[e] & 15)) ^ (R.F[g[e] >> 4] >> (g[e] & 15));
+                const uint32_t d = (__ldg(R.F + (rt[e] >> 4)) >> (rt[e] & 15)) ^ (__ldg(R.F + (g[e] >> 4)) >> (g[e] & 15));
                 if (d & 1u) {
                     const unsigned bitm = 1u << (14 + 16 * (g[e] & 1));
                     if (!(__ldcg(Lw + (g[e] >> 1)) & bitm)) atomicOr(Lw + (g[e] >> 1), bitm);
