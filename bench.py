@@ -66,10 +66,18 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
+    """Fingerprint of the kernel sources' code: comments and whitespace are
+    dropped, so an edit to a comment does not retire a traffic capture."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1612_08312_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        if not f.endswith((".cu", ".cuh", ".h")):
+            continue
+        text = open(os.path.join(csrc, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(f.encode() + b"\0" + " ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

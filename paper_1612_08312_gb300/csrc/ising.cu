@@ -10,11 +10,14 @@
 //                   compares its bytes with the threshold four at a time
 //                   (a satisfied bond is active with p = 1 - exp(-2 beta J),
 //                   the SW bond rule), then runs the tile-local labelling.
-//   ising_flip      resolves every site to its cluster root and flips the
-//                   site iff the root's flip bit is set.
-//   ising_measure   counts antiparallel bonds and -1 spins per tile (exact
-//                   integers; energy of Eq. 1, magnetisation of Eq. 2).
-//   boundary_kernel unites the clusters that cross tile faces (all models).
+//   ising_flip      flips every site whose cluster's flip bit is set: the
+//                   bit of its tile-local root, XOR that root's correction
+//                   bit where the cluster crosses a tile face.
+//   ising_measure   counts antiparallel bonds and -1 spins per tile, four
+//                   cells per thread (exact integers; energy of Eq. 1,
+//                   magnetisation of Eq. 2).
+//   boundary_kernel unites the clusters that cross tile faces and sets the
+//                   correction bits (all models).
 //   labels_kernel   writes the canonical label of every site on demand.
 #include <algorithm>
 
