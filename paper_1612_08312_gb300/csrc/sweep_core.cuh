@@ -96,11 +96,6 @@ __device__ __forceinline__ int vertex_local_cell(const TileCtx &c, int m)
     return c.t + ((m & 1) ? c.dxm : 0) + ((m & 2) ? c.dym : 0) + ((m & 4) ? c.dzm : 0);
 }
 
-__device__ __forceinline__ bool vertex_inside(const TileCtx &c, int m)
-{
-    return !(((m & 1) && c.bx) || ((m & 2) && c.by) || ((m & 4) && c.bz));
-}
-
 __device__ __forceinline__ int wrap_back(int v, int L) { return v == 0 ? L - 1 : v - 1; }
 
 // Cells of the backward halo staged by the tile kernels.

@@ -104,12 +104,6 @@ __device__ __forceinline__ uint64_t prob_threshold(float p)
     return t >= 4294967296.0f ? (1ull << 32) : (uint64_t)__float2ull_rz(t);
 }
 
-template <typename T>
-__host__ __device__ constexpr size_t vec_halo_bytes(int TX, int TY, int TZ)
-{
-    return (size_t)16 * (TX + 1) * (TY + 1) * (TZ + 1) * sizeof(T);
-}
-
 template <int NC, typename T>
 __global__ void __launch_bounds__(512) vec_local_kernel(const __grid_constant__ Batch B)
 {
