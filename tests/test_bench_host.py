@@ -1,0 +1,52 @@
+"""Host logic of bench.py: the kernel-code fingerprint that keys a committed
+DRAM-traffic capture, and the lookup of that capture."""
+import os
+import shutil
+
+import bench
+
+
+def copy_tree(tmp_path):
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(bench.ROOT, "paper_1612_08312_gb300", "csrc"),
+                    root / "paper_1612_08312_gb300" / "csrc",
+                    ignore=shutil.ignore_patterns("*.o", "*.so"))
+    (root / "profiles").mkdir()
+    return root
+
+
+def fingerprint(root):
+    old = bench.ROOT
+    bench.ROOT = str(root)
+    try:
+        return bench.kernel_source_hash()
+    finally:
+        bench.ROOT = old
+
+
+def test_fingerprint_ignores_comments_and_whitespace_but_not_code(tmp_path):
+    root = copy_tree(tmp_path)
+    base = fingerprint(root)
+    f = root / "paper_1612_08312_gb300" / "csrc" / "ising.cu"
+    text = f.read_text()
+    f.write_text("// a new comment line\n/* and a block\n   comment */\n" + text.replace("\n", "\n\n", 3))
+    assert fingerprint(root) == base
+    f.write_text(text.replace("MEASURE_BLOCK = 128", "MEASURE_BLOCK = 64"))
+    assert fingerprint(root) != base
+
+
+def test_committed_traffic_is_read_per_kernel_and_fingerprint(tmp_path):
+    root = copy_tree(tmp_path)
+    h = fingerprint(root)
+    (root / "profiles" / "traffic.txt").write_text(
+        "# kernel bytes_per_site source_hash\n"
+        f"ising_local_kernel 2.5 {h}\n"
+        "ising_flip_kernel 3.0 0000000000000000\n")
+    old = bench.ROOT
+    bench.ROOT = str(root)
+    try:
+        assert bench.committed_traffic("ising_local_kernel", 1000) == 2500.0
+        assert bench.committed_traffic("ising_flip_kernel", 1000) is None  # taken on other code
+        assert bench.committed_traffic("ising_measure_kernel", 1000) is None
+    finally:
+        bench.ROOT = old
