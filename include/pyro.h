@@ -93,7 +93,9 @@ typedef struct {
     double J;          /* ferromagnetic coupling, J > 0 (the paper uses J = 1) */
     uint64_t seed;     /* Philox key */
     void *stream;      /* cudaStream_t to run on; NULL = the library creates one */
-    int tile[3];       /* labelling tile in cells (each must divide L); {0,0,0} = default */
+    int tile[3];       /* labelling tile in cells: power-of-two edges, each dividing L, at most
+                          512 cells; {0,0,0} = default (Ising 8 x 8 x 4, n-vector 8 x 4 x 4,
+                          each edge reduced to the largest power of two dividing L) */
 } pyro_config;
 
 typedef struct {
