@@ -20,19 +20,6 @@ namespace pyro {
 // touch 32 consecutive words for any fixed s (no bank conflicts).
 __device__ __forceinline__ int lslot(int v, int nt) { return (v & 15) * nt + (v >> 4); }
 
-__device__ __forceinline__ int sfind(volatile int *lab, int x, int nt)
-{
-    int p = lab[lslot(x, nt)];
-#pragma unroll 1
-    for (int it = 0; p != x && it < 65536; ++it) {
-        const int gp = lab[lslot(p, nt)];
-        if (gp != p) lab[lslot(x, nt)] = gp;  // path halving; gp is an ancestor of x
-        x = p;
-        p = gp;
-    }
-    return x;
-}
-
 // Iteration bound of one union (4096).  A test can lower it (to 0) through
 // pyro_debug_set to exercise the bound-exceeded status path.
 static __constant__ int c_unite_bound = 4096;

@@ -406,10 +406,29 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
     }
     __syncthreads();  // all unions done
     if (!ok) atomicOr(&R.st->status, ST_NOCONVERGE);
-    // every site takes the root of its component's representative.  The
-    // representatives are this thread's own sites: each one's root is found
-    // (no unions any more, so the walk ends at the true root) and stored in
-    // its entry, which shortens the other threads' walks through it.
+    // every representative's entry moves to its grandparent, all of them
+    // together, until each points at its root (no unions any more, so the
+    // entries only move up their trees; the work is spread evenly over the
+    // threads, whatever the trees' depths)
+    volatile int *vl = s.lab;
+#pragma unroll 1
+    for (int it = 0; it < 64; ++it) {
+        int changed = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if ((reps >> q) & 1u) {
+                const int x = 16 * c.t + q;
+                const int p = vl[lslot(x, nt)];
+                const int gp = vl[lslot(p, nt)];
+                if (gp != p) {
+                    vl[lslot(x, nt)] = gp;
+                    changed = 1;
+                }
+            }
+        if (!__syncthreads_or(changed)) break;
+        if (it == 63) atomicOr(&R.st->status, ST_NOCONVERGE);
+    }
+    // every site takes the root of its component's representative
     uint32_t packed[8];
     uint32_t root0[4];
 #pragma unroll
@@ -423,15 +442,7 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
 #pragma unroll
             for (int u = 0; u < v; ++u)
                 if (rv == (uint32_t)u) r = root[u];
-            if (rv == (uint32_t)v) {
-                if (v == 0 && joined) {
-                    r = root0[f];
-                } else {
-                    const int x = 16 * c.t + 4 * f + v;
-                    r = (uint32_t)sfind(s.lab, x, nt);
-                    s.lab[lslot(x, nt)] = (int)r;
-                }
-            }
+            if (rv == (uint32_t)v) r = (v == 0 && joined) ? root0[f] : (uint32_t)vl[lslot(16 * c.t + 4 * f + v, nt)];
             root[v] = r;
         }
         if (f == 0) {
