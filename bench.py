@@ -399,7 +399,7 @@ def compare_plain_fp64(pyro, wl, args, obj, batched, value_fast):
     launches (no CUDA graph), the same number of sweeps; and the Binder
     ratio with its jackknife error from per-sweep traces of both forms."""
     import numpy as np
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from paper_1612_08312_gb300.fss import jackknife
     model = wl["model"]
     reps = [(L, T) for L in wl["Ls"] for T in wl["Ts"]] if batched else [(args.L or wl["L"], wl["T"])]
     lats = [pyro.Lattice(L, model, 7 + r, precision=pyro.FP64, start=wl["start"]) for r, (L, T) in enumerate(reps)]
@@ -431,8 +431,11 @@ def compare_plain_fp64(pyro, wl, args, obj, batched, value_fast):
         pyro.pyro_set_trace(lat.h, nb)
         lat.sweep(1.0 / T0, nb)
         tr = pyro.pyro_get_trace(lat.h, nb)
-        from refmath import jackknife_ratio
-        U, err = jackknife_ratio(tr[:, 1], tr[:, 2], 40)
+        nbin = 40
+        per = len(tr) // nbin
+        b2 = tr[: per * nbin, 1].reshape(nbin, per).mean(1)
+        b4 = tr[: per * nbin, 2].reshape(nbin, per).mean(1)
+        U, err, _ = jackknife(lambda a, b: b / (a * a), b2, b4)
         res[name] = {"U": U, "U_err": err}
         lat.close()
     for lat in lats:

@@ -199,8 +199,16 @@ int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int
  *   PYRO_DEBUG_UNITE_BOUND  iteration bound of one shared-memory union
  *                           (default 4096; 0 makes every union give up at
  *                           once, so the next synchronising call returns
- *                           PYRO_E_NOCONVERGE). */
-enum { PYRO_DEBUG_FAIL_ALLOCS = 1, PYRO_DEBUG_UNITE_BOUND = 2 };
+ *                           PYRO_E_NOCONVERGE);
+ *   PYRO_DEBUG_NOALLOC_STAMP  the stamp of the crossing-cluster links of the
+ *                           next pyro_ising_sweep_noalloc call on the current
+ *                           device (32-bit value), so that a test can take
+ *                           the calls across the stamps' wrap-around;
+ *   PYRO_DEBUG_EPOCH_START  the stamp that lattices and batches created from
+ *                           now on start their crossing-cluster links at
+ *                           (32-bit value; default 0), likewise. */
+enum { PYRO_DEBUG_FAIL_ALLOCS = 1, PYRO_DEBUG_UNITE_BOUND = 2, PYRO_DEBUG_NOALLOC_STAMP = 3,
+       PYRO_DEBUG_EPOCH_START = 4 };
 int pyro_debug_set(int key, int64_t value);
 
 /* Tracing: run n sweeps at beta like pyro_sweep, but as separate launches
@@ -236,8 +244,9 @@ const char *pyro_last_error(void);
  * loads the library and stays there until the process exits.
  *
  *   spins_in   device, L^3 uint16 in the compact layout of pyro_get_state
- *   spins_out  device, L^3 uint16: the spins after the sweep (may equal
- *              spins_in for an in-place update)
+ *   spins_out  device, L^3 uint16: the spins after the sweep; either equal
+ *              to spins_in (an in-place update) or not overlapping it, else
+ *              PYRO_E_INVAL
  *   labels     device, 16 L^3 int32: canonical cluster labels of the sweep
  *   meas       device, 4 doubles: E, m^2, m^4 and M of the new configuration
  *   L          1 <= L <= PYRO_NOALLOC_MAX_L, else PYRO_E_INVAL

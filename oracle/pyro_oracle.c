@@ -15,7 +15,7 @@
  *     embedded-cluster (reflection) form for n = 2, 3.
  *   - Eq. 2: the moment ratio U = <m^4>/<m^2>^2 with m = M/N.
  *
- * Conventions that the paper leaves open (all listed in the design doc):
+ * Conventions that the paper leaves open:
  *   - site index i = 16*(x + L*(y + L*z)) + 4*f + mu, position (quarter
  *     units) 4*(x,y,z) + A_f + B_mu;
  *   - bonds grouped by tetrahedron: bond 12*r + k, r = i >> 2 the FCC point,

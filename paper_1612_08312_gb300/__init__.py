@@ -246,7 +246,7 @@ def pyro_launch_count(h) -> int:
     return int(lib().pyro_launch_count(h))
 
 
-DEBUG_FAIL_ALLOCS, DEBUG_UNITE_BOUND = 1, 2
+DEBUG_FAIL_ALLOCS, DEBUG_UNITE_BOUND, DEBUG_NOALLOC_STAMP, DEBUG_EPOCH_START = 1, 2, 3, 4
 
 
 def pyro_set_graphs(h, on: bool):

@@ -140,6 +140,7 @@ static int measure_of(Engine &e, int r, double *E, double *m2, double *m4)
 }
 
 cudaError_t ising_set_unite_bound(int bound);
+int noalloc_set_stamp(uint32_t stamp);
 cudaError_t vec_set_unite_bound(int bound);
 
 // ------------------------------------------------------------- autotuner --
@@ -490,6 +491,16 @@ int pyro_debug_set(int key, int64_t value)
     if (key == PYRO_DEBUG_FAIL_ALLOCS) {
         if (value < 0) return fail(PYRO_E_INVAL, "count must be >= 0");
         g_fail_allocs = (int)value;
+        return PYRO_OK;
+    }
+    if (key == PYRO_DEBUG_NOALLOC_STAMP) {
+        if (value < 0 || value > 0xFFFFFFFFll) return fail(PYRO_E_INVAL, "stamp must be a 32-bit value");
+        if (noalloc_set_stamp((uint32_t)value)) return fail(PYRO_E_CUDA, "no current device");
+        return PYRO_OK;
+    }
+    if (key == PYRO_DEBUG_EPOCH_START) {
+        if (value < 0 || value > 0xFFFFFFFFll) return fail(PYRO_E_INVAL, "stamp must be a 32-bit value");
+        g_epoch_start = (uint64_t)value;
         return PYRO_OK;
     }
     if (key == PYRO_DEBUG_UNITE_BOUND) {

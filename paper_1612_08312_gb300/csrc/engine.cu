@@ -136,6 +136,7 @@ void launch_accumulate(const Batch &B, bool ising, int mode, int nc, cudaStream_
 
 // ------------------------------------------------------------------ host --
 int g_fail_allocs = 0;
+uint64_t g_epoch_start = 0;
 
 static cudaError_t engine_malloc(void **p, size_t bytes)
 {
@@ -243,6 +244,7 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
     B.lTY = log2i(t.TY);
     B.lTZ = log2i(t.TZ);
     reps.assign(R, Rep{});
+    epoch = g_epoch_start;
     ntiles = 0;
     nblocks = 0;
     const int nt = t.TX * t.TY * t.TZ;
@@ -281,6 +283,10 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
         }
         e = cudaMemsetAsync(p.st, 0, sizeof(DevStats), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(p.P, 0xFF, (size_t)p.N * sizeof(unsigned long long), stream);
+        if (e == cudaSuccess && g_epoch_start) {
+            hst_epoch = g_epoch_start;
+            e = cudaMemcpyAsync(&p.st->epoch, &hst_epoch, sizeof(hst_epoch), cudaMemcpyHostToDevice, stream);
+        }
         if (e != cudaSuccess) return e;
     }
     B.tile_begin[R] = ntiles;

@@ -34,6 +34,7 @@ struct Engine {
     std::vector<GraphEntry> graphs;
     uint64_t sweep = 0;
     uint64_t epoch = 0;  // host mirror of the device epoch (same for all replicas)
+    uint64_t hst_epoch = 0;  // staging word of the initial epoch copy
     uint64_t launches = 0;
     bool labels_valid = false;
 
@@ -65,6 +66,10 @@ uint64_t ising_threshold(double beta, double J);
 // Test hooks (pyro_debug_set): the next `fail_allocs` device allocations
 // of an engine set-up report failure.
 extern int g_fail_allocs;
+// Test hook (pyro_debug_set): the crossing-link stamp that engines created
+// from now on start at (0 by default), so that a test can take a chain
+// across the stamps' wrap-around.
+extern uint64_t g_epoch_start;
 TileShape default_tile(const int *Ls, int R, int model);
 std::string check_tile(const int *Ls, int R, int model, int prec, const TileShape &t);
 size_t local_smem(int model, int prec, const TileShape &t);

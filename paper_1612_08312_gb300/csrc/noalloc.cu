@@ -63,6 +63,22 @@ __global__ void na_setup_kernel(Rep rep, Rep *rep_slot, DevStats *st, unsigned l
     *st = z;
 }
 
+}  // namespace
+
+// Test hook (pyro_debug_set): the stamp of the next call's links on the
+// current device, so that a test can take the calls across the stamps'
+// wrap-around.
+int noalloc_set_stamp(uint32_t stamp)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return -1;
+    std::lock_guard<std::mutex> lock(na_mutex);
+    na_epoch[dev] = stamp;
+    return 0;
+}
+
+namespace {
+
 int na_fail(int code, const std::string &msg)
 {
     set_error(msg);
@@ -148,7 +164,11 @@ extern "C" int pyro_ising_sweep_noalloc(const uint16_t *spins_in, uint16_t *spin
     B.block_begin[1] = (rep.ncells + CELL_BLOCK - 1) / CELL_BLOCK;
 
     if (spins_in != spins_out) {
-        e = cudaMemcpyAsync(spins_out, spins_in, (size_t)rep.ncells * sizeof(uint16_t), cudaMemcpyDeviceToDevice, s);
+        const size_t nb = (size_t)rep.ncells * sizeof(uint16_t);
+        const uintptr_t a = reinterpret_cast<uintptr_t>(spins_in), b = reinterpret_cast<uintptr_t>(spins_out);
+        if (a < b + nb && b < a + nb)
+            return na_fail(PYRO_E_INVAL, "pyro_ising_sweep_noalloc: spins_in and spins_out overlap without being equal");
+        e = cudaMemcpyAsync(spins_out, spins_in, nb, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return na_fail(PYRO_E_CUDA, std::string("spin copy: ") + cudaGetErrorString(e));
     }
     na_setup_kernel<<<1, 1, 0, s>>>(rep, reinterpret_cast<Rep *>(base + NA_OFF_REP), rep.st, sweep, epoch);

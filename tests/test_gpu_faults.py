@@ -51,3 +51,23 @@ def test_autotuned_tile_is_valid_and_exact(model):
     o.sweep(0.25, 2)
     assert (g.labels() == o.labels()).all()
     assert np.abs(g.spins().astype(np.float64) - o.spins()).max() <= 1e-12
+
+
+def test_chain_crosses_the_link_stamp_wraparound():
+    """Links of clusters that cross tile faces are stamped with a per-sweep
+    epoch; before the 32-bit stamps would wrap, every link array is cleared
+    and the epochs restart.  A lattice started just below that point must
+    follow the oracle's chain bit for bit through it, with single sweeps and
+    with a multi-sweep call."""
+    try:
+        pyro.pyro_debug_set(pyro.DEBUG_EPOCH_START, 0xFFFFFFF0 - 3)
+        g = pyro.Lattice(16, pyro.ISING, 9, start="random")
+    finally:
+        pyro.pyro_debug_set(pyro.DEBUG_EPOCH_START, 0)
+    o = oracle.Oracle(16, oracle.ISING, 9, "random")
+    for n in (1, 1, 1, 1, 1, 3, 40):
+        g.sweep(1 / 4.21394, n)
+        o.sweep(1 / 4.21394, n)
+        assert (g.spins() == o.spins()).all()
+        assert (g.labels() == o.labels()).all()
+    g.close()

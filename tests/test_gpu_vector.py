@@ -10,12 +10,12 @@ FP32: spins stored and updated in float against the FP64 oracle, from an
 FP32-representable start.  A bond decision may differ only where the
 uniform lies within 2^-20 of the FP64 probability (a near tie); when no
 decision differs the energy after one sweep must agree to 1e-6 relative."""
-import math
 
 import numpy as np
 import pytest
 
 import oracle
+import refmath
 import paper_1612_08312_gb300 as pyro
 import workloads
 
@@ -74,8 +74,11 @@ def test_fp64_accumulators(model):
 
 
 def near_ties(model, L, T, seed, s0, sweep_index):
-    """Bonds of one sweep whose uniform lies within 2^-20 of the FP64
-    probability, recomputed from the oracle's configuration."""
+    """Bonds of one sweep whose 32-bit uniform w lies within 2^12 of the FP64
+    threshold floor(p 2^32) (a window of 2^-20 in probability), with w drawn
+    the way the sweep draws it: the bond's random-number id, the top byte
+    from its BOND-stream byte and the low 24 bits from its TIE-stream word,
+    recomputed with cuRAND's Philox from the oracle's configuration."""
     o = oracle.Oracle(L, model, seed, "up")
     o.set_spins(s0)
     o.sweep_count = sweep_index
@@ -85,13 +88,9 @@ def near_ties(model, L, T, seed, s0, sweep_index):
     proj = s0 @ r
     x = proj[bi] * proj[bj]
     idx = np.nonzero(x > 0)[0]
-    key = [seed & 0xFFFFFFFF, seed >> 32]
-    ties = 0
-    for b in idx.tolist():
-        w = oracle.philox([(b >> 2) & 0xFFFFFFFF, b >> 34, sweep_index, 1], key)[b & 3]
-        u = (float(w) + 0.5) / 2 ** 32
-        p = -math.expm1(-2 / T * x[b])
-        ties += abs(u - p) < 2 ** -20
+    w = refmath.bond_words_of(seed, sweep_index, idx).astype(np.float64)
+    thr = np.floor(-np.expm1(-2 / T * x[idx]) * 2.0 ** 32)
+    ties = int((np.abs(w - thr) < 2.0 ** 12).sum())
     return o, ties
 
 
