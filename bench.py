@@ -252,6 +252,8 @@ def main():
     ap.add_argument("--ref-L", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 arm of n-vector workloads")
+    ap.add_argument("--binder-sweeps", type=int, default=8000,
+                    help="sweeps of each form's Binder-ratio trace (200 bins) in the n-vector comparison")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -278,12 +280,15 @@ def main():
     if batched:
         reps = [(L, T) for L in wl["Ls"] for T in wl["Ts"]]
         Ls, betas = [r[0] for r in reps], [1.0 / r[1] for r in reps]
-        obj = pyro.Replicas(Ls, betas, model, precision=prec, start=wl["start"], seed=rank_seed(wl["seed"], rank))
+        btile = "auto" if args.tile == "auto" else ((0, 0, 0) if args.tile == "default" else
+                                                    tuple(int(v) for v in args.tile.split("x")))
+        obj = pyro.Replicas(Ls, betas, model, precision=prec, start=wl["start"], seed=rank_seed(wl["seed"], rank),
+                            tile=btile)
         N = obj.total_sites
         stream = torch.cuda.ExternalStream(obj.stream)
         sweep = lambda n: obj.sweep(n)
         sync = obj.sync
-        tile = None
+        tile = list(obj.tile)
     else:
         L = args.L or wl["L"]
         beta = 1.0 / wl["T"]
@@ -369,21 +374,22 @@ def main():
                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 24, "steps": args.e2e_steps}
     else:
         # a batch's state stays on the device; per step the host reads every
-        # replica's measurement
+        # replica's measurement (one device-to-host copy)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             obj.sweep(1)
-            for r in range(len(reps)):
-                obj.measure(r)
+            obj.measure_all()
         e2e_s = reduce_max(time.perf_counter() - t0, world, device="cuda")
         out["e2e"] = {"value": N * args.e2e_steps * world / (e2e_s * 1e9), "unit": UNIT,
-                      "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 24 * len(reps), "steps": args.e2e_steps}
+                      "h2d_bytes_per_step": 0,
+                      # one copy of the replicas' contiguous 152-byte device records
+                      "d2h_bytes_per_step": 152 * len(reps), "steps": args.e2e_steps}
 
     # n-vector workloads: the plain FP64 form (per-replica launches, no
     # graph) on the same sweeps, and the Binder ratio from both chains
     if model != 1 and not args.no_compare and rank == 0:
-        out["vs_plain_fp64"] = compare_plain_fp64(pyro, wl, args, obj, batched, value)
+        out["vs_plain_fp64"] = compare_plain_fp64(pyro, wl, args, obj, batched, value, ms / args.steps)
 
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
@@ -394,10 +400,18 @@ def main():
         dist.destroy_process_group()
 
 
-def compare_plain_fp64(pyro, wl, args, obj, batched, value_fast):
-    """Time the plain form: FP64 spins, one lattice per replica, separate
-    launches (no CUDA graph), the same number of sweeps; and the Binder
-    ratio with its jackknife error from per-sweep traces of both forms."""
+def compare_plain_fp64(pyro, wl, args, obj, batched, value_fast, ms_fast):
+    """The plain form beside the fast one: FP64 spins, one lattice per
+    replica, separate launches (no CUDA graph), the same number of sweeps;
+    and the Binder ratio U = <m^4>/<m^2>^2 (Eq. 2) of one replica from
+    long per-sweep traces of both forms (200 bins, jackknife errors; the
+    smallest lattice of a batch, at its temperature nearest T_c), so
+    that the time each form needs to reach the same error on U can be
+    compared: sweeps needed scale with the squared error at a fixed sweep
+    count, so time-to-equal-error ratio = (plain ms per sweep x plain error^2)
+    / (fast ms per sweep x fast error^2).  The fast chain is a single FP32
+    lattice with graphs: a replica of a batch runs exactly the chain of a
+    single lattice with its seed."""
     import numpy as np
     from paper_1612_08312_gb300.fss import jackknife
     model = wl["model"]
@@ -417,32 +431,35 @@ def compare_plain_fp64(pyro, wl, args, obj, batched, value_fast):
     for lat in lats:
         lat.sync()
     dt = time.perf_counter() - t0
-    total = sum(16 * L ** 3 for L, _ in reps)
-    value_plain = total * n / (dt * 1e9)
-    # Binder ratio of the smallest replica from both forms (same sweep count)
-    L0, T0 = reps[0]
-    fast = pyro.Lattice(L0, model, 11, precision=pyro.FP32, start=wl["start"])
-    plain = pyro.Lattice(L0, model, 13, precision=pyro.FP64, start=wl["start"])
-    plain.set_graphs(False)
-    nb = 4000
-    res = {}
-    for name, lat in (("fp32_graph", fast), ("fp64_plain", plain)):
-        lat.sweep(1.0 / T0, 200)
-        pyro.pyro_set_trace(lat.h, nb)
-        lat.sweep(1.0 / T0, nb)
-        tr = pyro.pyro_get_trace(lat.h, nb)
-        nbin = 40
-        per = len(tr) // nbin
-        b2 = tr[: per * nbin, 1].reshape(nbin, per).mean(1)
-        b4 = tr[: per * nbin, 2].reshape(nbin, per).mean(1)
-        U, err, _ = jackknife(lambda a, b: b / (a * a), b2, b4)
-        res[name] = {"U": U, "U_err": err}
-        lat.close()
     for lat in lats:
         lat.close()
+    total = sum(16 * L ** 3 for L, _ in reps)
+    value_plain = total * n / (dt * 1e9)
+    ms_plain = dt * 1e3 / n
+    # Binder ratio from both forms at equal sweep counts, on the smallest
+    # lattice at the temperature nearest the workload's critical one
+    L0, T0 = min(reps, key=lambda lt: (lt[0], abs(lt[1] - wl["T"])))
+    eq, nbin, per = 500, 200, args.binder_sweeps // 200
+    res = {}
+    for name, prec, graphs, seed in (("fp32_graph", pyro.FP32, True, 11), ("fp64_plain", pyro.FP64, False, 13)):
+        lat = pyro.Lattice(L0, model, seed, precision=prec, start=wl["start"])
+        lat.set_graphs(graphs)
+        lat.sweep(1.0 / T0, eq)
+        pyro.pyro_set_trace(lat.h, nbin * per)
+        lat.sweep(1.0 / T0, nbin * per)
+        tr = pyro.pyro_get_trace(lat.h, nbin * per)
+        lat.close()
+        b2 = tr[:, 1].reshape(nbin, per).mean(1)
+        b4 = tr[:, 2].reshape(nbin, per).mean(1)
+        U, err, _ = jackknife(lambda a, b: b / (a * a), b2, b4)
+        res[name] = {"U": float(U), "U_err": float(err)}
+    ef, ep = res["fp32_graph"]["U_err"], res["fp64_plain"]["U_err"]
     return {"value": value_plain, "unit": UNIT, "ratio": value_fast / value_plain, "sweeps": n,
+            "ms_per_sweep": ms_plain,
             "form": "FP64 spins, one lattice per replica, one launch per phase (no graph)",
-            "binder": {"L": L0, "T": T0, "sweeps": nb, **res}}
+            "binder": {"L": L0, "T": T0, "equilibration": eq, "sweeps": nbin * per, "bins": nbin, **res,
+                       "error_ratio_plain_over_fast": ep / ef if ef > 0 else None},
+            "time_to_equal_error_ratio": (ms_plain * ep * ep) / (ms_fast * ef * ef) if ef > 0 else None}
 
 
 if __name__ == "__main__":

@@ -96,6 +96,14 @@ typedef struct {
     int tile[3];       /* labelling tile in cells: power-of-two edges, each dividing L, at most
                           512 cells; {0,0,0} = default (Ising 8 x 8 x 4, n-vector 8 x 4 x 4,
                           each edge reduced to the largest power of two dividing L) */
+    void *workspace;   /* NULL = the library allocates (and frees) the lattice's device memory;
+                          else caller-owned device memory (for instance a torch tensor's data_ptr),
+                          at least pyro_workspace_bytes(cfg) bytes, 256-byte aligned, from which
+                          every device array of the lattice is carved; the library frees none of
+                          it, and it must stay valid until pyro_destroy.  It opens with the
+                          statistics record, padded to 256 bytes; the spins follow at byte 256
+                          in the layout of pyro_get_state */
+    size_t workspace_bytes; /* size of workspace in bytes */
 } pyro_config;
 
 typedef struct {
@@ -114,8 +122,19 @@ typedef struct {
  * owned by the caller until pyro_destroy.  Sec. 2 (lattice), Eq. 1. */
 int pyro_init(pyro_handle *out, int L, int model, uint64_t seed);
 
-/* Same with every option of pyro_config.  cfg is read, not kept. */
+/* Same with every option of pyro_config.  cfg is read, not kept.  With a
+ * workspace, PYRO_E_NOMEM if it is smaller than pyro_workspace_bytes(cfg),
+ * PYRO_E_INVAL if it is not 256-byte aligned; no device allocation is made
+ * (pyro_set_trace alone allocates its ring buffer). */
 int pyro_init_ex(pyro_handle *out, const pyro_config *cfg);
+
+/* Device bytes of a lattice created with cfg (its spins, tile-local labels,
+ * crossing-cluster links, flip words, face masks, statistics, canonical
+ * labels, partial sums and replica record; Sec. 2 lattice of N = 16 L^3
+ * sites), for a caller that owns the device memory and passes it in
+ * cfg->workspace.  cfg->workspace itself is ignored.  0 if cfg is invalid
+ * (pyro_last_error says why). */
+size_t pyro_workspace_bytes(const pyro_config *cfg);
 
 /* Enqueue n Swendsen-Wang sweeps at inverse temperature beta (Sec. 2) on
  * the handle's stream; each sweep is followed by the measurement of Eq. 2,
@@ -277,8 +296,28 @@ int pyro_ising_sweep_noalloc(const uint16_t *spins_in, uint16_t *spins_out, int3
  * pyro_config.  Independent runs (Sec. 2: five independent runs). */
 int pyro_batch_init(pyro_batch *out, int R, const int *L, const double *beta, int model,
                     int precision, int start, uint64_t seed);
+
+/* Same with a labelling tile for every replica (power-of-two edges dividing
+ * every L; NULL or {0,0,0} = the default of the lattices' common divisor),
+ * e.g. from pyro_batch_autotune. */
+int pyro_batch_init_ex(pyro_batch *out, int R, const int *L, const double *beta, int model,
+                       int precision, int start, uint64_t seed, const int tile[3]);
+
+/* Autotuner for a batch: equilibrates R replicas (sizes L, inverse
+ * temperatures beta) with the default tile for 60 sweeps, then replays the
+ * same nsweeps sweeps with every candidate tile and returns the fastest in
+ * tile_out and its device ms per batch sweep.  Cached per (GPU name, the set
+ * of distinct L, model, precision) like pyro_autotune.  Allocates and frees
+ * scratch batches; synchronises. */
+int pyro_batch_autotune(int R, const int *L, const double *beta, int model, int precision, int nsweeps,
+                        int tile_out[3], double *ms_per_sweep);
 int pyro_batch_sweep(pyro_batch b, int n);
 int pyro_batch_stats(pyro_batch b, int r, pyro_stats_t *s);
+/* Every replica's statistics in s[0 .. R) and every replica's instantaneous
+ * E, m^2, m^4 in out[3 r + 0..2], each with one device-to-host copy (the
+ * replicas' records are contiguous on the device).  Synchronise. */
+int pyro_batch_stats_all(pyro_batch b, pyro_stats_t *s);
+int pyro_batch_measure_all(pyro_batch b, double *out);
 int pyro_batch_reset_stats(pyro_batch b);
 int pyro_batch_measure(pyro_batch b, int r, double *E, double *m2, double *m4);
 int pyro_batch_get_spins(pyro_batch b, int r, void *host, size_t bytes);

@@ -40,7 +40,8 @@ class PyroError(RuntimeError):
 class pyro_config(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("model", ctypes.c_int), ("precision", ctypes.c_int),
                 ("start", ctypes.c_int), ("J", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int * 3)]
+                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int * 3), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
 
 
 class pyro_stats_t(ctypes.Structure):
@@ -51,6 +52,7 @@ class pyro_stats_t(ctypes.Structure):
 _SIGS = {
     "pyro_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
     "pyro_init_ex": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(pyro_config)]),
+    "pyro_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(pyro_config)]),
     "pyro_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
     "pyro_measure": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_double)] * 3),
     "pyro_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pyro_stats_t)]),
@@ -82,6 +84,15 @@ _SIGS = {
     "pyro_batch_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
+    "pyro_batch_init_ex": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                          ctypes.POINTER(ctypes.c_int)]),
+    "pyro_batch_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "pyro_batch_stats_all": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pyro_batch_measure_all": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "pyro_batch_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pyro_batch_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(pyro_stats_t)]),
     "pyro_batch_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
@@ -138,11 +149,23 @@ def pyro_init(L: int, model: int, seed: int):
 
 
 def pyro_init_ex(L: int, model: int, seed: int, precision: int = FP32, start: int = START_UP,
-                 J: float = 1.0, stream: int | None = None, tile=(0, 0, 0)):
-    cfg = pyro_config(L, model, precision, start, J, seed, stream, (ctypes.c_int * 3)(*tile))
+                 J: float = 1.0, stream: int | None = None, tile=(0, 0, 0), workspace: int | None = None,
+                 workspace_bytes: int = 0):
+    cfg = pyro_config(L, model, precision, start, J, seed, stream, (ctypes.c_int * 3)(*tile), workspace,
+                      workspace_bytes)
     h = ctypes.c_void_p()
     _check(lib().pyro_init_ex(ctypes.byref(h), ctypes.byref(cfg)))
     return h
+
+
+def pyro_workspace_bytes(L: int, model: int, precision: int = FP32, start: int = START_UP, J: float = 1.0,
+                         tile=(0, 0, 0)) -> int:
+    """Device bytes of a lattice with this configuration (caller-owned memory)."""
+    cfg = pyro_config(L, model, precision, start, J, 0, None, (ctypes.c_int * 3)(*tile), None, 0)
+    n = int(lib().pyro_workspace_bytes(ctypes.byref(cfg)))
+    if n == 0:
+        raise PyroError(E_INVAL, lib().pyro_last_error().decode())
+    return n
 
 
 def pyro_sweep(h, beta: float, n: int = 1):
@@ -293,6 +316,40 @@ def pyro_batch_init(Ls, betas, model: int, precision: int = FP32, start: int = S
     return b
 
 
+def pyro_batch_init_ex(Ls, betas, model: int, precision: int = FP32, start: int = START_RANDOM, seed: int = 1,
+                       tile=(0, 0, 0)):
+    R = len(Ls)
+    La = (ctypes.c_int * R)(*Ls)
+    Ba = (ctypes.c_double * R)(*betas)
+    b = ctypes.c_void_p()
+    _check(lib().pyro_batch_init_ex(ctypes.byref(b), R, La, Ba, model, precision, start, seed,
+                                    (ctypes.c_int * 3)(*tile)))
+    return b
+
+
+def pyro_batch_autotune(Ls, betas, model: int, precision: int = FP32, nsweeps: int = 3):
+    """Fastest labelling tile for a batch of these sizes (cached); returns
+    (tile, ms per batch sweep)."""
+    R = len(Ls)
+    t = (ctypes.c_int * 3)()
+    ms = ctypes.c_double()
+    _check(lib().pyro_batch_autotune(R, (ctypes.c_int * R)(*Ls), (ctypes.c_double * R)(*betas), model, precision,
+                                     nsweeps, t, ctypes.byref(ms)))
+    return tuple(t), ms.value
+
+
+def pyro_batch_stats_all(b, R: int) -> list:
+    s = (pyro_stats_t * R)()
+    _check(lib().pyro_batch_stats_all(b, ctypes.cast(s, ctypes.c_void_p)))
+    return [_stats_dict(x) for x in s]
+
+
+def pyro_batch_measure_all(b, R: int) -> np.ndarray:
+    out = np.zeros((R, 3), dtype=np.float64)
+    _check(lib().pyro_batch_measure_all(b, _buf(out)))
+    return out
+
+
 def pyro_batch_sweep(b, n: int = 1):
     _check(lib().pyro_batch_sweep(b, n))
 
@@ -354,12 +411,16 @@ class Lattice:
     """One pyrochlore lattice on the GPU (owns a pyro_handle)."""
 
     def __init__(self, L: int, model: int = ISING, seed: int = 1, precision: int = FP32,
-                 start: str | int = "up", J: float = 1.0, tile=(0, 0, 0), stream: int | None = None):
+                 start: str | int = "up", J: float = 1.0, tile=(0, 0, 0), stream: int | None = None,
+                 workspace: int | None = None, workspace_bytes: int = 0):
+        """workspace: a device pointer (e.g. a torch tensor's data_ptr()) of
+        at least pyro_workspace_bytes(...) bytes that the lattice lives in;
+        the caller keeps it alive until close()."""
         st = start if isinstance(start, int) else (START_RANDOM if start == "random" else START_UP)
         self.L, self.model, self.seed, self.precision = L, model, seed, precision
         if tile == "auto":
             tile = pyro_autotune(L, model, precision)[0]
-        self.h = pyro_init_ex(L, model, seed, precision, st, J, stream, tile)
+        self.h = pyro_init_ex(L, model, seed, precision, st, J, stream, tile, workspace, workspace_bytes)
         self.N = pyro_num_sites(self.h)
 
     def close(self):
@@ -421,10 +482,13 @@ class Replicas:
     """Independent lattices updated together (owns a pyro_batch)."""
 
     def __init__(self, Ls, betas, model: int = ISING, precision: int = FP32, start: str | int = "random",
-                 seed: int = 1):
+                 seed: int = 1, tile=(0, 0, 0)):
         st = start if isinstance(start, int) else (START_RANDOM if start == "random" else START_UP)
         self.Ls, self.betas, self.model = list(Ls), list(betas), model
-        self.b = pyro_batch_init(self.Ls, self.betas, model, precision, st, seed)
+        if tile == "auto":
+            tile = pyro_batch_autotune(self.Ls, self.betas, model, precision)[0]
+        self.tile = tuple(tile)
+        self.b = pyro_batch_init_ex(self.Ls, self.betas, model, precision, st, seed, tile)
         self.total_sites = pyro_batch_total_sites(self.b)
 
     def close(self):
@@ -449,6 +513,13 @@ class Replicas:
 
     def measure(self, r: int):
         return pyro_batch_measure(self.b, r)
+
+    def stats_all(self) -> list:
+        return pyro_batch_stats_all(self.b, len(self.Ls))
+
+    def measure_all(self) -> np.ndarray:
+        """(R, 3) array of every replica's E, m^2, m^4 (one device read)."""
+        return pyro_batch_measure_all(self.b, len(self.Ls))
 
     def spins(self, r: int):
         return pyro_batch_get_spins(self.b, r, 16 * self.Ls[r] ** 3, self.model)

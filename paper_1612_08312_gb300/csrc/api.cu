@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -48,25 +49,41 @@ static int finish(Engine &e)
 
 static bool beta_ok(double b) { return b >= 0.0 && std::isfinite(b); }
 
-static int create(Engine &e, int R, const int *Ls, const double *betas, int model, int prec, int start, double J,
-                  const uint64_t *seeds, void *stream, const int tile[3])
+// Argument checks and the resolved tile of a set of lattices; "" if valid.
+static std::string check_args(int R, const int *Ls, const double *betas, int model, int prec, int start, double J,
+                              const int tile[3], TileShape &t)
 {
-    if (R < 1 || R > MAX_REPS) return fail(PYRO_E_INVAL, "number of replicas must be in [1, 64]");
+    if (R < 1 || R > MAX_REPS) return "number of replicas must be in [1, 64]";
     for (int r = 0; r < R; ++r) {
-        if (Ls[r] < 1 || Ls[r] > PYRO_MAX_L) return fail(PYRO_E_INVAL, "L must be in [1, 511]");
-        if (betas && !beta_ok(betas[r])) return fail(PYRO_E_INVAL, "beta must be finite and >= 0");
+        if (Ls[r] < 1 || Ls[r] > PYRO_MAX_L) return "L must be in [1, 511]";
+        if (betas && !beta_ok(betas[r])) return "beta must be finite and >= 0";
     }
-    if (model < PYRO_ISING || model > PYRO_HEIS) return fail(PYRO_E_INVAL, "model must be 1, 2 or 3");
-    if (prec != PYRO_FP32 && prec != PYRO_FP64) return fail(PYRO_E_INVAL, "precision must be PYRO_FP32 or PYRO_FP64");
-    if (start != PYRO_START_UP && start != PYRO_START_RANDOM)
-        return fail(PYRO_E_INVAL, "start must be PYRO_START_UP or PYRO_START_RANDOM");
-    if (!(J > 0.0) || !std::isfinite(J)) return fail(PYRO_E_INVAL, "J must be positive and finite");
-    TileShape t = default_tile(Ls, R, model);
+    if (model < PYRO_ISING || model > PYRO_HEIS) return "model must be 1, 2 or 3";
+    if (prec != PYRO_FP32 && prec != PYRO_FP64) return "precision must be PYRO_FP32 or PYRO_FP64";
+    if (start != PYRO_START_UP && start != PYRO_START_RANDOM) return "start must be PYRO_START_UP or PYRO_START_RANDOM";
+    if (!(J > 0.0) || !std::isfinite(J)) return "J must be positive and finite";
+    t = default_tile(Ls, R, model);
     if (tile && (tile[0] || tile[1] || tile[2])) t = TileShape{tile[0], tile[1], tile[2]};
-    const std::string why = check_tile(Ls, R, model, prec, t);
+    return check_tile(Ls, R, model, prec, t);
+}
+
+static int create(Engine &e, int R, const int *Ls, const double *betas, int model, int prec, int start, double J,
+                  const uint64_t *seeds, void *stream, const int tile[3], void *workspace = nullptr,
+                  size_t workspace_bytes_ = 0)
+{
+    TileShape t;
+    const std::string why = check_args(R, Ls, betas, model, prec, start, J, tile, t);
     if (!why.empty()) return fail(PYRO_E_INVAL, why);
     std::string err;
-    const cudaError_t ce = e.setup(R, Ls, betas, model, prec, start, J, seeds, static_cast<cudaStream_t>(stream), t, err);
+    if (workspace) {
+        if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(PYRO_E_INVAL, "workspace must be 256-byte aligned");
+        const size_t need = workspace_bytes(R, Ls, model, model == PYRO_ISING ? PYRO_FP64 : prec, t);
+        if (workspace_bytes_ < need)
+            return fail(PYRO_E_NOMEM, "workspace too small: " + std::to_string(workspace_bytes_) + " bytes, " +
+                                          std::to_string(need) + " needed");
+    }
+    const cudaError_t ce = e.setup(R, Ls, betas, model, prec, start, J, seeds, static_cast<cudaStream_t>(stream), t, err,
+                                   workspace, workspace_bytes_);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         e.release();
@@ -126,6 +143,38 @@ static int reset_stats(Engine &e)
     return PYRO_OK;
 }
 
+// Every replica's statistics (DevStats records are contiguous): one
+// device-to-host copy.
+static int stats_all(Engine &e, pyro_stats_t *s)
+{
+    std::vector<DevStats> d((size_t)e.R);
+    PYRO_CUDA(cudaMemcpyAsync(d.data(), e.reps[0].st, d.size() * sizeof(DevStats), cudaMemcpyDeviceToHost, e.stream),
+              "stats copy");
+    const int rc = finish(e);
+    if (rc) return rc;
+    for (int r = 0; r < e.R; ++r) {
+        s[r].count = d[r].count;
+        double *dst[5] = {&s[r].sum_E, &s[r].sum_E2, &s[r].sum_m2, &s[r].sum_m4, &s[r].sum_absm};
+        for (int k = 0; k < 5; ++k) *dst[k] = d[r].acc_s[k] + d[r].acc_c[k];
+    }
+    return PYRO_OK;
+}
+
+// Every replica's instantaneous E, m^2, m^4 (out[3 r + 0..2]): one
+// measurement launch over all replicas and one device-to-host copy.
+static int measure_all(Engine &e, double *out)
+{
+    PYRO_CUDA(e.measure(), "measure launch");
+    std::vector<DevStats> d((size_t)e.R);
+    PYRO_CUDA(cudaMemcpyAsync(d.data(), e.reps[0].st, d.size() * sizeof(DevStats), cudaMemcpyDeviceToHost, e.stream),
+              "measure copy");
+    const int rc = finish(e);
+    if (rc) return rc;
+    for (int r = 0; r < e.R; ++r)
+        for (int k = 0; k < 3; ++k) out[3 * r + k] = d[r].last[k];
+    return PYRO_OK;
+}
+
 static int measure_of(Engine &e, int r, double *E, double *m2, double *m4)
 {
     PYRO_CUDA(e.measure(), "measure launch");
@@ -144,7 +193,8 @@ int noalloc_set_stamp(uint32_t stamp);
 cudaError_t vec_set_unite_bound(int bound);
 
 // ------------------------------------------------------------- autotuner --
-// Candidate tiles: powers of two, 64 to 512 cells, each edge dividing L.
+// Candidate tiles: powers of two, 64 to 512 cells, each edge dividing L
+// (for a set of lattices, their greatest common divisor).
 static std::vector<TileShape> tile_candidates(int L, int model)
 {
     std::vector<TileShape> out;
@@ -161,7 +211,7 @@ static std::vector<TileShape> tile_candidates(int L, int model)
 }
 
 static std::mutex tune_mutex;
-static std::map<std::tuple<std::string, int, int, int>, std::pair<TileShape, double>> tune_cache;
+static std::map<std::tuple<std::string, std::string, int, int>, std::pair<TileShape, double>> tune_cache;
 
 static std::string device_name()
 {
@@ -176,19 +226,21 @@ static std::string device_name()
 }
 
 // Optional file cache named by PYRO_AUTOTUNE_CACHE: lines
-// "<gpu> <L> <model> <precision> <TX> <TY> <TZ> <ms>".
-static bool file_lookup(const std::string &gpu, int L, int model, int prec, TileShape &t, double &ms)
+// "<gpu> <sizes> <model> <precision> <TX> <TY> <TZ> <ms>", sizes the
+// lattice's L or a batch's distinct L joined by commas.
+static bool file_lookup(const std::string &gpu, const std::string &L, int model, int prec, TileShape &t, double &ms)
 {
     const char *path = std::getenv("PYRO_AUTOTUNE_CACHE");
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
     char name[256];
-    int l, m, p, tx, ty, tz;
+    int m, p, tx, ty, tz;
     double v;
     bool found = false;
-    while (std::fscanf(f, "%255s %d %d %d %d %d %d %lf", name, &l, &m, &p, &tx, &ty, &tz, &v) == 8)
-        if (gpu == name && l == L && m == model && p == prec) {
+    char sizes[256];
+    while (std::fscanf(f, "%255s %255s %d %d %d %d %d %lf", name, sizes, &m, &p, &tx, &ty, &tz, &v) == 8)
+        if (gpu == name && L == sizes && m == model && p == prec) {
             t = TileShape{tx, ty, tz};
             ms = v;
             found = true;
@@ -197,13 +249,13 @@ static bool file_lookup(const std::string &gpu, int L, int model, int prec, Tile
     return found;
 }
 
-static void file_store(const std::string &gpu, int L, int model, int prec, const TileShape &t, double ms)
+static void file_store(const std::string &gpu, const std::string &L, int model, int prec, const TileShape &t, double ms)
 {
     const char *path = std::getenv("PYRO_AUTOTUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d %d %d %d %.6f\n", gpu.c_str(), L, model, prec, t.TX, t.TY, t.TZ, ms);
+    std::fprintf(f, "%s %s %d %d %d %d %d %.6f\n", gpu.c_str(), L.c_str(), model, prec, t.TX, t.TY, t.TZ, ms);
     std::fclose(f);
 }
 
@@ -223,13 +275,30 @@ int pyro_init_ex(pyro_handle *out, const pyro_config *cfg)
     if (!h) return fail(PYRO_E_NOMEM, "host allocation failed");
     const double beta0 = 0.0;
     const int rc = create(h->e, 1, &cfg->L, &beta0, cfg->model, cfg->precision, cfg->start, cfg->J, &cfg->seed,
-                          cfg->stream, cfg->tile);
+                          cfg->stream, cfg->tile, cfg->workspace, cfg->workspace_bytes);
     if (rc) {
         delete h;
         return rc;
     }
     *out = h;
     return PYRO_OK;
+}
+
+size_t pyro_workspace_bytes(const pyro_config *cfg)
+{
+    if (!cfg) {
+        set_error("NULL argument");
+        return 0;
+    }
+    const double beta0 = 0.0;
+    TileShape t;
+    const std::string why =
+        check_args(1, &cfg->L, &beta0, cfg->model, cfg->precision, cfg->start, cfg->J, cfg->tile, t);
+    if (!why.empty()) {
+        set_error(why);
+        return 0;
+    }
+    return workspace_bytes(1, &cfg->L, cfg->model, cfg->model == PYRO_ISING ? PYRO_FP64 : cfg->precision, t);
 }
 
 int pyro_init(pyro_handle *out, int L, int model, uint64_t seed)
@@ -418,50 +487,77 @@ int pyro_set_graphs(pyro_handle h, int on)
     return PYRO_OK;
 }
 
-int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int tile_out[3], double *ms_per_sweep)
+}  // extern "C"
+
+namespace pyro {
+
+// Fastest tile for a set of R lattices (sizes Ls, inverse temperatures
+// betas): equilibrate them with the default tile, then replay the same
+// sweeps from that state with every candidate tile.  The chain does not
+// depend on the tile, so every candidate does identical work.
+static int autotune_set(int R, const int *Ls, const double *betas, int model, int precision, int nsweeps,
+                        int tile_out[3], double *ms_per_sweep)
 {
-    if (!tile_out) return fail(PYRO_E_INVAL, "NULL argument");
-    if (L < 1 || L > PYRO_MAX_L) return fail(PYRO_E_INVAL, "L must be in [1, 511]");
+    if (!tile_out || !Ls || !betas) return fail(PYRO_E_INVAL, "NULL argument");
+    if (R < 1 || R > MAX_REPS) return fail(PYRO_E_INVAL, "number of replicas must be in [1, 64]");
+    int g = 0;
+    std::vector<int> sizes;
+    for (int r = 0; r < R; ++r) {
+        if (Ls[r] < 1 || Ls[r] > PYRO_MAX_L) return fail(PYRO_E_INVAL, "L must be in [1, 511]");
+        if (!beta_ok(betas[r])) return fail(PYRO_E_INVAL, "beta must be >= 0");
+        int a = g, b = Ls[r];
+        while (b) {
+            const int t = a % b;
+            a = b;
+            b = t;
+        }
+        g = a;
+        sizes.push_back(Ls[r]);
+    }
     if (model < PYRO_ISING || model > PYRO_HEIS) return fail(PYRO_E_INVAL, "model must be 1, 2 or 3");
     if (precision != PYRO_FP32 && precision != PYRO_FP64) return fail(PYRO_E_INVAL, "bad precision");
-    if (!beta_ok(beta) || nsweeps < 1) return fail(PYRO_E_INVAL, "beta must be >= 0 and nsweeps >= 1");
+    if (nsweeps < 1) return fail(PYRO_E_INVAL, "nsweeps must be >= 1");
     const int prec = model == PYRO_ISING ? PYRO_FP64 : precision;
+    std::sort(sizes.begin(), sizes.end());
+    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+    std::string skey;
+    for (size_t k = 0; k < sizes.size(); ++k) skey += (k ? "," : "") + std::to_string(sizes[k]);
     const std::string gpu = device_name();
     std::lock_guard<std::mutex> lock(tune_mutex);
-    const auto key = std::make_tuple(gpu, L, model, prec);
-    TileShape best = default_tile(&L, 1, model);
+    const auto key = std::make_tuple(gpu, skey, model, prec);
+    TileShape best = default_tile(Ls, R, model);
     double best_ms = -1.0;
     auto it = tune_cache.find(key);
     if (it != tune_cache.end()) {
         best = it->second.first;
         best_ms = it->second.second;
-    } else if (!file_lookup(gpu, L, model, prec, best, best_ms)) {
-        // Equilibrate one lattice with the default tile, then replay the same
-        // sweeps from that state with every candidate tile: the chain does
-        // not depend on the tile, so every candidate does identical work.
-        const uint64_t seed = 0x5EEDull;
+    } else if (!file_lookup(gpu, skey, model, prec, best, best_ms)) {
+        std::vector<uint64_t> seeds((size_t)R);
+        for (int r = 0; r < R; ++r) seeds[r] = 0x5EEDull + (uint64_t)r * 0x9E3779B97F4A7C15ull;
         const int warm = 60;
         Engine ref;
         std::string err;
-        const TileShape t0 = default_tile(&L, 1, model);
-        if (ref.setup(1, &L, &beta, model, prec, PYRO_START_RANDOM, 1.0, &seed, nullptr, t0, err) != cudaSuccess ||
+        const TileShape t0 = default_tile(Ls, R, model);
+        if (ref.setup(R, Ls, betas, model, prec, PYRO_START_RANDOM, 1.0, seeds.data(), nullptr, t0, err) != cudaSuccess ||
             ref.sweeps(warm) != cudaSuccess || cudaStreamSynchronize(ref.stream) != cudaSuccess) {
             cudaGetLastError();
             ref.release();
-            return fail(PYRO_E_CUDA, "autotune: reference lattice failed");
+            return fail(PYRO_E_CUDA, "autotune: reference lattices failed");
         }
-        for (const TileShape &t : tile_candidates(L, model)) {
-            if (!check_tile(&L, 1, model, prec, t).empty()) continue;
+        for (const TileShape &t : tile_candidates(g, model)) {
+            if (!check_tile(Ls, R, model, prec, t).empty()) continue;
             Engine e;
-            if (e.setup(1, &L, &beta, model, prec, PYRO_START_RANDOM, 1.0, &seed, nullptr, t, err) != cudaSuccess) {
+            if (e.setup(R, Ls, betas, model, prec, PYRO_START_RANDOM, 1.0, seeds.data(), nullptr, t, err) != cudaSuccess) {
                 cudaGetLastError();
                 e.release();
                 continue;
             }
             e.use_graphs = false;
             double ms = 0.0;
-            cudaError_t ce = cudaMemcpyAsync(e.reps[0].spins, ref.reps[0].spins, ref.spin_bytes(0),
-                                             cudaMemcpyDeviceToDevice, e.stream);
+            cudaError_t ce = cudaSuccess;
+            for (int r = 0; r < R && ce == cudaSuccess; ++r)
+                ce = cudaMemcpyAsync(e.reps[r].spins, ref.reps[r].spins, ref.spin_bytes(r), cudaMemcpyDeviceToDevice,
+                                     e.stream);
             if (ce == cudaSuccess) ce = e.set_sweep(ref.sweep);
             if (ce == cudaSuccess) ce = e.sweeps(1);
             if (ce == cudaSuccess) ce = e.time_sweeps(nsweeps, ms);
@@ -476,7 +572,7 @@ int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int
             }
         }
         ref.release();
-        if (best_ms >= 0.0) file_store(gpu, L, model, prec, best, best_ms);
+        if (best_ms >= 0.0) file_store(gpu, skey, model, prec, best, best_ms);
     }
     tune_cache[key] = std::make_pair(best, best_ms);
     tile_out[0] = best.TX;
@@ -484,6 +580,22 @@ int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int
     tile_out[2] = best.TZ;
     if (ms_per_sweep) *ms_per_sweep = best_ms;
     return PYRO_OK;
+}
+
+}  // namespace pyro
+
+extern "C" {
+
+int pyro_autotune(int L, int model, int precision, double beta, int nsweeps, int tile_out[3], double *ms_per_sweep)
+{
+    if (!tile_out) return fail(PYRO_E_INVAL, "NULL argument");
+    return autotune_set(1, &L, &beta, model, precision, nsweeps, tile_out, ms_per_sweep);
+}
+
+int pyro_batch_autotune(int R, const int *L, const double *beta, int model, int precision, int nsweeps, int tile_out[3],
+                        double *ms_per_sweep)
+{
+    return autotune_set(R, L, beta, model, precision, nsweeps, tile_out, ms_per_sweep);
 }
 
 int pyro_debug_set(int key, int64_t value)
@@ -535,6 +647,12 @@ void pyro_destroy(pyro_handle h)
 int pyro_batch_init(pyro_batch *out, int R, const int *L, const double *beta, int model, int precision, int start,
                     uint64_t seed)
 {
+    return pyro_batch_init_ex(out, R, L, beta, model, precision, start, seed, nullptr);
+}
+
+int pyro_batch_init_ex(pyro_batch *out, int R, const int *L, const double *beta, int model, int precision, int start,
+                       uint64_t seed, const int tile[3])
+{
     if (!out || !L || !beta) return fail(PYRO_E_INVAL, "NULL argument");
     *out = nullptr;
     if (R < 1 || R > MAX_REPS) return fail(PYRO_E_INVAL, "number of replicas must be in [1, 64]");
@@ -542,7 +660,7 @@ int pyro_batch_init(pyro_batch *out, int R, const int *L, const double *beta, in
     for (int r = 0; r < R; ++r) seeds[r] = seed + (uint64_t)r * 0x9E3779B97F4A7C15ull;
     pyro_batch_ctx *b = new (std::nothrow) pyro_batch_ctx();
     if (!b) return fail(PYRO_E_NOMEM, "host allocation failed");
-    const int rc = create(b->e, R, L, beta, model, precision, start, 1.0, seeds.data(), nullptr, nullptr);
+    const int rc = create(b->e, R, L, beta, model, precision, start, 1.0, seeds.data(), nullptr, tile);
     if (rc) {
         delete b;
         return rc;
@@ -563,6 +681,18 @@ int pyro_batch_stats(pyro_batch b, int r, pyro_stats_t *s)
 {
     if (!b || !s || r < 0 || r >= b->e.R) return fail(PYRO_E_INVAL, "bad argument");
     return stats_of(b->e, r, s);
+}
+
+int pyro_batch_stats_all(pyro_batch b, pyro_stats_t *s)
+{
+    if (!b || !s) return fail(PYRO_E_INVAL, "NULL argument");
+    return stats_all(b->e, s);
+}
+
+int pyro_batch_measure_all(pyro_batch b, double *out)
+{
+    if (!b || !out) return fail(PYRO_E_INVAL, "NULL argument");
+    return measure_all(b->e, out);
 }
 
 int pyro_batch_reset_stats(pyro_batch b)

@@ -215,9 +215,52 @@ static size_t spin_bytes_of(int model, int prec, int64_t N)
 
 size_t Engine::spin_bytes(int r) const { return spin_bytes_of(model, prec, reps[r].N); }
 
-cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_, int prec_, int start_, double J,
-                          const uint64_t *seeds, cudaStream_t user_stream, const TileShape &t, std::string &err)
+static size_t ws_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// The replicas' statistics records (contiguous); per replica: spins,
+// links, tile-local labels, flip words, face masks, canonical labels; then
+// the tiles' partial sums and the replica table.
+size_t workspace_bytes(int R, const int *Ls, int model, int prec, const TileShape &t)
 {
+    size_t total = ws_align((size_t)R * sizeof(DevStats));
+    int64_t ntiles = 0;
+    const int nt = t.TX * t.TY * t.TZ;
+    for (int r = 0; r < R; ++r) {
+        const int64_t ncells = (int64_t)Ls[r] * Ls[r] * Ls[r], N = 16 * ncells;
+        total += ws_align(spin_bytes_of(model, prec, N)) + ws_align((size_t)N * sizeof(unsigned long long)) +
+                 ws_align((size_t)N * sizeof(uint16_t)) + ws_align((size_t)ncells * sizeof(uint16_t)) +
+                 ws_align((size_t)ncells * sizeof(uint32_t)) + ws_align((size_t)N * sizeof(int32_t));
+        ntiles += ncells / nt;
+    }
+    return total + ws_align((size_t)ntiles * 4 * sizeof(double)) + ws_align((size_t)R * sizeof(Rep));
+}
+
+// One device array: carved from the caller's workspace when there is one,
+// else allocated (and freed by release()).
+cudaError_t Engine::alloc(void **p, size_t bytes)
+{
+    if (ws) {
+        const size_t need = ws_align(bytes);
+        if (ws_used + need > ws_bytes) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        *p = ws + ws_used;
+        ws_used += need;
+        return cudaSuccess;
+    }
+    const cudaError_t e = engine_malloc(p, bytes);
+    if (e == cudaSuccess) owned.push_back(*p);
+    return e;
+}
+
+cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_, int prec_, int start_, double J,
+                          const uint64_t *seeds, cudaStream_t user_stream, const TileShape &t, std::string &err,
+                          void *workspace, size_t workspace_bytes_)
+{
+    ws = static_cast<unsigned char *>(workspace);
+    ws_bytes = workspace ? workspace_bytes_ : 0;
+    ws_used = 0;
     R = R_;
     model = model_;
     prec = model_ == PYRO_ISING ? PYRO_FP64 : prec_;
@@ -248,6 +291,14 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
     ntiles = 0;
     nblocks = 0;
     const int nt = t.TX * t.TY * t.TZ;
+    // every replica's statistics in one block, so that they can be read in
+    // one copy
+    DevStats *stats = nullptr;
+    e = alloc((void **)&stats, (size_t)R * sizeof(DevStats));
+    if (e != cudaSuccess) {
+        err = ws ? "workspace too small" : "device allocation failed";
+        return e;
+    }
     for (int r = 0; r < R; ++r) {
         Rep &p = reps[r];
         p.L = Ls[r];
@@ -272,14 +323,15 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
                   {(void **)&p.L16, (size_t)p.N * sizeof(uint16_t)},
                   {(void **)&p.F, (size_t)p.ncells * sizeof(uint16_t)},
                   {(void **)&p.dmask, (size_t)p.ncells * sizeof(uint32_t)},
-                  {(void **)&p.st, sizeof(DevStats)}};
+                  {(void **)&p.labels, ws ? (size_t)p.N * sizeof(int32_t) : 0}};
+        p.st = stats + r;
         for (auto &a : al) {
-            e = engine_malloc(a.ptr, a.bytes);
+            if (!a.bytes) continue;  // canonical labels: allocated on first use, unless in a workspace
+            e = alloc(a.ptr, a.bytes);
             if (e != cudaSuccess) {
-                err = "device allocation failed";
+                err = ws ? "workspace too small" : "device allocation failed";
                 return e;
             }
-            owned.push_back(*a.ptr);
         }
         e = cudaMemsetAsync(p.st, 0, sizeof(DevStats), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(p.P, 0xFF, (size_t)p.N * sizeof(unsigned long long), stream);
@@ -291,18 +343,12 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
     }
     B.tile_begin[R] = ntiles;
     B.block_begin[R] = nblocks;
-    e = engine_malloc((void **)&B.partials, (size_t)ntiles * 4 * sizeof(double));
+    e = alloc((void **)&B.partials, (size_t)ntiles * 4 * sizeof(double));
+    if (e == cudaSuccess) e = alloc((void **)&d_reps, (size_t)R * sizeof(Rep));
     if (e != cudaSuccess) {
-        err = "device allocation failed";
+        err = ws ? "workspace too small" : "device allocation failed";
         return e;
     }
-    owned.push_back(B.partials);
-    e = engine_malloc((void **)&d_reps, (size_t)R * sizeof(Rep));
-    if (e != cudaSuccess) {
-        err = "device allocation failed";
-        return e;
-    }
-    owned.push_back(d_reps);
     B.reps = d_reps;
     e = cudaMemcpyAsync(d_reps, reps.data(), (size_t)R * sizeof(Rep), cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return e;
@@ -565,21 +611,16 @@ cudaError_t Engine::set_trace(int r, int64_t cap)
 
 int Engine::read_status(std::string &err)
 {
-    int st = 0;
-    for (int r = 0; r < R; ++r) {
-        int s = 0;
-        cudaError_t e = cudaMemcpyAsync(&s, &reps[r].st->status, sizeof(int), cudaMemcpyDeviceToHost, stream);
-        if (e != cudaSuccess) {
-            err = cudaGetErrorString(e);
-            return -1;
-        }
-        e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) {
-            err = cudaGetErrorString(e);
-            return -1;
-        }
-        st |= s;
+    // the replicas' records are contiguous: one copy reads every status
+    std::vector<DevStats> d((size_t)R);
+    cudaError_t e = cudaMemcpyAsync(d.data(), reps[0].st, d.size() * sizeof(DevStats), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        err = cudaGetErrorString(e);
+        return -1;
     }
+    int st = 0;
+    for (const auto &x : d) st |= x.status;
     return st;
 }
 

@@ -38,8 +38,15 @@ struct Engine {
     uint64_t launches = 0;
     bool labels_valid = false;
 
+    // caller-owned device memory, if any: every array is carved from it
+    // (256-byte aligned, in the order of workspace_bytes) and nothing is freed
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0, ws_used = 0;
+
     cudaError_t setup(int R, const int *Ls, const double *betas, int model, int prec, int start, double J,
-                      const uint64_t *seeds, cudaStream_t user_stream, const TileShape &t, std::string &err);
+                      const uint64_t *seeds, cudaStream_t user_stream, const TileShape &t, std::string &err,
+                      void *workspace = nullptr, size_t workspace_bytes = 0);
+    cudaError_t alloc(void **p, size_t bytes);
     void release();
     size_t spin_bytes(int r) const;
     cudaError_t set_beta(int r, double beta);
@@ -71,6 +78,9 @@ extern int g_fail_allocs;
 // across the stamps' wrap-around.
 extern uint64_t g_epoch_start;
 TileShape default_tile(const int *Ls, int R, int model);
+// Device bytes of every array of a set of lattices (labels included), as
+// the engine lays them out in a caller-owned workspace.
+size_t workspace_bytes(int R, const int *Ls, int model, int prec, const TileShape &t);
 std::string check_tile(const int *Ls, int R, int model, int prec, const TileShape &t);
 size_t local_smem(int model, int prec, const TileShape &t);
 

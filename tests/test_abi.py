@@ -88,3 +88,15 @@ def test_debug_hook_rejects_bad_keys_without_a_gpu():
     with pytest.raises(pyro.PyroError):
         pyro.pyro_debug_set(pyro.DEBUG_FAIL_ALLOCS, -1)
     pyro.pyro_debug_set(pyro.DEBUG_FAIL_ALLOCS, 0)
+
+
+def test_workspace_bytes_is_host_only_and_checks_its_config():
+    # the size of a lattice's device arrays is computed on the host
+    n8 = pyro.pyro_workspace_bytes(8, pyro.ISING)
+    n16 = pyro.pyro_workspace_bytes(16, pyro.ISING)
+    assert n8 > 0 and 7 * n8 < n16 < 9 * n8
+    assert pyro.pyro_workspace_bytes(8, pyro.XY, pyro.FP64) > pyro.pyro_workspace_bytes(8, pyro.XY, pyro.FP32)
+    with pytest.raises(pyro.PyroError):
+        pyro.pyro_workspace_bytes(0, pyro.ISING)
+    with pytest.raises(pyro.PyroError):
+        pyro.pyro_workspace_bytes(8, pyro.ISING, tile=(3, 1, 1))

@@ -55,3 +55,24 @@ def test_mixed_sizes_uneven_tiles():
         o = oracle.Oracle(L, oracle.ISING, pyro.replica_seed(2, r), "random")
         o.sweep(1 / 4.21394, 5)
         assert (b.spins(r) == o.spins()).all()
+
+
+def test_batch_tile_autotune_and_single_reads():
+    """A batch created with the batch autotuner's tile runs the same chains;
+    all replicas' statistics and measurements come back in one read each and
+    equal the per-replica reads."""
+    Ls = [8, 16, 24]
+    betas = [1 / 4.2, 1 / 4.21394, 1 / 4.23]
+    tile, ms = pyro.pyro_batch_autotune(Ls, betas, pyro.ISING, pyro.FP64, 2)
+    assert all(L % t == 0 for L in Ls for t in tile) and ms > 0
+    b = pyro.Replicas(Ls, betas, pyro.ISING, start="random", seed=4, tile=tile)
+    b.sweep(6)
+    allm = b.measure_all()
+    alls = b.stats_all()
+    for r, L in enumerate(Ls):
+        o = oracle.Oracle(L, oracle.ISING, pyro.replica_seed(4, r), "random")
+        o.sweep(betas[r], 6)
+        assert (b.spins(r) == o.spins()).all()
+        assert tuple(allm[r]) == o.measure() == b.measure(r)
+        assert alls[r] == o.stats() == b.stats(r)
+    b.close()
