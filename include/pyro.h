@@ -274,7 +274,7 @@ const char *pyro_last_error(void);
  *
  * Calls no cudaMalloc, cudaFree or other allocating routine.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture.  Every
+ * and caches it.  Every
  * call on a device uses the same array, which keeps the previous call's
  * contents; the call re-initialises what must start from zero.  Calls whose
  * work overlaps on the GPU (other streams, other host threads) race on the
@@ -326,6 +326,82 @@ int64_t pyro_batch_total_sites(pyro_batch b);
 void *pyro_batch_get_stream(pyro_batch b);
 uint64_t pyro_batch_launch_count(pyro_batch b);
 void pyro_batch_destroy(pyro_batch b);
+
+/* ---- generic lattices: a bond list, a neighbour table or the simple-cubic
+ *      lattice, optionally diluted ------------------------------------------
+ *
+ * Sec. 2: the SW program needs only the table of every site's nearest
+ * neighbours, so the same sweep runs on any lattice given as a list of
+ * bonds.  Sec. 3.4 (Eq. 5-6) compares with the simple-cubic lattice (also
+ * coordination six); Sec. 4 names diluted lattices as the extension.
+ *
+ * Conventions (the pyrochlore ones above, with these changes):
+ *   bond id      bond e of the list joins sites bond_i[e] and bond_j[e]; its
+ *                random-number id is e, its uniform w_e as above.  Listing
+ *                the pyrochlore bonds in the order of their ids above gives
+ *                the pyrochlore chain of the same seed, bit for bit;
+ *   simple cubic L^3 sites, site i = x + L (y + L z), bond 3 i + d joins i
+ *                to the next site along axis d (periodic), L >= 2;
+ *   dilution     a vacant site takes no part: bonds touching it are absent,
+ *                it is a cluster of its own and never flips; a bond with mask
+ *                0 is absent; absent bonds are never active and are left out
+ *                of E;
+ *   measurement  E = -J sum over present bonds of s_i . s_j, m = |M| / N_occ,
+ *                M summed over occupied sites (m = 0 if none is occupied).
+ * Errors, streams and statistics as for pyro_handle. */
+typedef struct pyro_graph_ctx *pyro_graph;
+
+typedef struct {
+    int model;                /* PYRO_ISING, PYRO_XY or PYRO_HEIS */
+    int precision;            /* n-vector spins: PYRO_FP32 or PYRO_FP64 (ignored for Ising) */
+    int start;                /* PYRO_START_UP or PYRO_START_RANDOM (per site as for pyro_handle) */
+    double J;                 /* ferromagnetic coupling, J > 0 */
+    uint64_t seed;            /* Philox key */
+    void *stream;             /* cudaStream_t; NULL = the library creates one */
+    int sc_L;                 /* > 0: the simple-cubic sc_L^3 lattice (2 <= sc_L <= 1290), bonds
+                                 implicit; bond_i, bond_j must then be NULL */
+    int64_t nsites;           /* sc_L = 0: number of sites N, 1 <= N < 2^31 */
+    int64_t nbonds;           /* sc_L = 0: number of bonds, 0 <= nbonds < 2^35 */
+    const int32_t *bond_i;    /* sc_L = 0: host, nbonds sites in [0, N) */
+    const int32_t *bond_j;    /* sc_L = 0: host, nbonds sites in [0, N), bond_j[e] != bond_i[e] */
+    const uint8_t *site_mask; /* host, N bytes, 0 = vacant; NULL = every site occupied */
+    const uint8_t *bond_mask; /* host, one byte per bond, 0 = absent; NULL = every bond present */
+} pyro_graph_config;
+
+/* Create a generic lattice; the host arrays are read, not kept (the bond
+ * list is copied to the device).  PYRO_E_INVAL on a bad argument (a site
+ * out of range, a self-loop, sizes out of range). */
+int pyro_graph_init(pyro_graph *out, const pyro_graph_config *cfg);
+
+/* Bond list of a neighbour table nbr (N rows of z entries, -1 = none;
+ * Sec. 2): slot (i, k) with i < nbr[i z + k] is a bond, in the order of
+ * (i, k).  Returns the number of bonds and, if bond_i and bond_j are not
+ * NULL, writes them; PYRO_E_INVAL if an entry is out of range or names its
+ * own row, or if j does not appear in i's row as often as i in j's row.
+ * Host only; no GPU is needed. */
+int64_t pyro_graph_bonds_from_table(int64_t N, int z, const int32_t *nbr, int32_t *bond_i, int32_t *bond_j);
+
+/* n sweeps at inverse temperature beta (as pyro_sweep). */
+int pyro_graph_sweep(pyro_graph g, double beta, int64_t n);
+/* E, m^2, m^4 of the current configuration.  Synchronises. */
+int pyro_graph_measure(pyro_graph g, double *E, double *m2, double *m4);
+int pyro_graph_stats(pyro_graph g, pyro_stats_t *s);
+int pyro_graph_reset_stats(pyro_graph g);
+/* Spins in site order: Ising int8 +-1 (N bytes); n-vector doubles, site-
+ * major (8 n N bytes).  Vacant sites' spins are kept and returned as well. */
+int pyro_graph_get_spins(pyro_graph g, void *host, size_t bytes);
+int pyro_graph_set_spins(pyro_graph g, const void *host, size_t bytes);
+/* Canonical cluster labels of the last sweep (N int32; before the first
+ * sweep every site is its own cluster). */
+int pyro_graph_get_labels(pyro_graph g, int32_t *host, int64_t n);
+int pyro_graph_set_sweep(pyro_graph g, uint64_t sweep);
+uint64_t pyro_graph_get_sweep(pyro_graph g);
+int64_t pyro_graph_num_sites(pyro_graph g);
+int64_t pyro_graph_num_bonds(pyro_graph g);
+int pyro_graph_sync(pyro_graph g);
+void *pyro_graph_get_stream(pyro_graph g);
+uint64_t pyro_graph_launch_count(pyro_graph g);
+void pyro_graph_destroy(pyro_graph g);
 
 #ifdef __cplusplus
 }

@@ -147,6 +147,13 @@ static uint64_t prob_threshold(double p)
     return (uint64_t)t;
 }
 
+/* Exported forms of the two helpers above, for graph_oracle.c. */
+uint64_t orc_prob_threshold(double p) { return prob_threshold(p); }
+uint32_t orc_stream_bit(uint64_t seed, uint32_t sweep_field, uint32_t tag, uint64_t x)
+{
+    return stream_bit(seed, sweep_field, tag, x);
+}
+
 /* Ising: a satisfied bond is active with p = 1 - exp(-2 beta J)
  * (Swendsen-Wang bond probability; SW87 as cited in Sec. 1). */
 uint64_t orc_threshold(double beta, double J)

@@ -44,6 +44,14 @@ class pyro_config(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t)]
 
 
+class pyro_graph_config(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("precision", ctypes.c_int), ("start", ctypes.c_int),
+                ("J", ctypes.c_double), ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+                ("sc_L", ctypes.c_int), ("nsites", ctypes.c_int64), ("nbonds", ctypes.c_int64),
+                ("bond_i", ctypes.c_void_p), ("bond_j", ctypes.c_void_p), ("site_mask", ctypes.c_void_p),
+                ("bond_mask", ctypes.c_void_p)]
+
+
 class pyro_stats_t(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint64), ("sum_E", ctypes.c_double), ("sum_E2", ctypes.c_double),
                 ("sum_m2", ctypes.c_double), ("sum_m4", ctypes.c_double), ("sum_absm", ctypes.c_double)]
@@ -103,6 +111,24 @@ _SIGS = {
     "pyro_batch_launch_count": (ctypes.c_uint64, [ctypes.c_void_p]),
     "pyro_batch_get_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
     "pyro_batch_destroy": (None, [ctypes.c_void_p]),
+    "pyro_graph_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(pyro_graph_config)]),
+    "pyro_graph_bonds_from_table": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                     ctypes.c_void_p]),
+    "pyro_graph_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64]),
+    "pyro_graph_measure": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_double)] * 3),
+    "pyro_graph_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pyro_stats_t)]),
+    "pyro_graph_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
+    "pyro_graph_get_spins": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "pyro_graph_set_spins": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "pyro_graph_get_labels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "pyro_graph_set_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "pyro_graph_get_sweep": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "pyro_graph_num_sites": (ctypes.c_int64, [ctypes.c_void_p]),
+    "pyro_graph_num_bonds": (ctypes.c_int64, [ctypes.c_void_p]),
+    "pyro_graph_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "pyro_graph_get_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
+    "pyro_graph_launch_count": (ctypes.c_uint64, [ctypes.c_void_p]),
+    "pyro_graph_destroy": (None, [ctypes.c_void_p]),
     "pyro_ising_sweep_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                                                 ctypes.c_void_p]),
@@ -406,6 +432,117 @@ def pyro_ising_sweep_noalloc(spins_in: int, spins_out: int, labels: int, meas: i
     _check(lib().pyro_ising_sweep_noalloc(spins_in, spins_out, labels, meas, L, beta, seed, sweep, stream))
 
 
+# ---------------------------------------------------- generic lattices --
+def pyro_graph_bonds_from_table(nbr: np.ndarray):
+    """Bond list (bond_i, bond_j) of a symmetric neighbour table (N x z,
+    -1 = none): slot (i, k) with i < nbr[i, k], in the order of (i, k)."""
+    t = np.ascontiguousarray(nbr, dtype=np.int32)
+    N, z = t.shape
+    E = int(lib().pyro_graph_bonds_from_table(N, z, _buf(t), None, None))
+    if E < 0:
+        _check(E)
+    bi = np.zeros(max(E, 1), dtype=np.int32)
+    bj = np.zeros(max(E, 1), dtype=np.int32)
+    rc = int(lib().pyro_graph_bonds_from_table(N, z, _buf(t), _buf(bi), _buf(bj)))
+    if rc < 0:
+        _check(rc)
+    return bi[:E], bj[:E]
+
+
+def pyro_graph_init(model: int, seed: int, precision: int = FP64, start: int = START_UP, J: float = 1.0,
+                    stream: int | None = None, sc_L: int = 0, nsites: int = 0, bond_i=None, bond_j=None,
+                    site_mask=None, bond_mask=None):
+    keep = []
+
+    def arr(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    bi = arr(bond_i, np.int32)
+    bj = arr(bond_j, np.int32)
+    nb = 0 if bond_i is None else len(keep[0])
+    cfg = pyro_graph_config(model, precision, start, J, seed, stream, sc_L, nsites, nb, bi, bj,
+                            arr(site_mask, np.uint8), arr(bond_mask, np.uint8))
+    g = ctypes.c_void_p()
+    _check(lib().pyro_graph_init(ctypes.byref(g), ctypes.byref(cfg)))
+    return g
+
+
+def pyro_graph_sweep(g, beta: float, n: int = 1):
+    _check(lib().pyro_graph_sweep(g, beta, n))
+
+
+def pyro_graph_measure(g):
+    E, m2, m4 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().pyro_graph_measure(g, ctypes.byref(E), ctypes.byref(m2), ctypes.byref(m4)))
+    return E.value, m2.value, m4.value
+
+
+def pyro_graph_stats(g) -> dict:
+    s = pyro_stats_t()
+    _check(lib().pyro_graph_stats(g, ctypes.byref(s)))
+    return dict(count=s.count, sum_E=s.sum_E, sum_E2=s.sum_E2, sum_m2=s.sum_m2, sum_m4=s.sum_m4,
+                sum_absm=s.sum_absm)
+
+
+def pyro_graph_reset_stats(g):
+    _check(lib().pyro_graph_reset_stats(g))
+
+
+def pyro_graph_num_sites(g) -> int:
+    return int(lib().pyro_graph_num_sites(g))
+
+
+def pyro_graph_num_bonds(g) -> int:
+    return int(lib().pyro_graph_num_bonds(g))
+
+
+def pyro_graph_get_spins(g, model: int) -> np.ndarray:
+    N = pyro_graph_num_sites(g)
+    out = np.zeros(N, dtype=np.int8) if model == ISING else np.zeros((N, model), dtype=np.float64)
+    _check(lib().pyro_graph_get_spins(g, _buf(out), out.nbytes))
+    return out
+
+
+def pyro_graph_set_spins(g, s: np.ndarray, model: int):
+    a = np.ascontiguousarray(s, dtype=np.int8 if model == ISING else np.float64)
+    _check(lib().pyro_graph_set_spins(g, _buf(a), a.nbytes))
+
+
+def pyro_graph_get_labels(g) -> np.ndarray:
+    N = pyro_graph_num_sites(g)
+    out = np.zeros(N, dtype=np.int32)
+    _check(lib().pyro_graph_get_labels(g, _buf(out), N))
+    return out
+
+
+def pyro_graph_set_sweep(g, s: int):
+    _check(lib().pyro_graph_set_sweep(g, s))
+
+
+def pyro_graph_get_sweep(g) -> int:
+    return int(lib().pyro_graph_get_sweep(g))
+
+
+def pyro_graph_sync(g):
+    _check(lib().pyro_graph_sync(g))
+
+
+def pyro_graph_get_stream(g) -> int:
+    return lib().pyro_graph_get_stream(g) or 0
+
+
+def pyro_graph_launch_count(g) -> int:
+    return int(lib().pyro_graph_launch_count(g))
+
+
+def pyro_graph_destroy(g):
+    lib().pyro_graph_destroy(g)
+
+
 # ------------------------------------------------------- convenience API --
 class Lattice:
     """One pyrochlore lattice on the GPU (owns a pyro_handle)."""
@@ -539,3 +676,70 @@ class Replicas:
 def replica_seed(seed: int, r: int) -> int:
     """Seed of replica r of a batch: seed + r * 0x9E3779B97F4A7C15 mod 2^64."""
     return (seed + r * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+
+
+class Graph:
+    """A generic lattice on the GPU (owns a pyro_graph): an explicit bond
+    list (bond_i, bond_j) over nsites sites, or the simple-cubic sc_L^3
+    lattice, optionally diluted by a site mask and a bond mask."""
+
+    def __init__(self, model: int = ISING, seed: int = 1, precision: int = FP64, start: str | int = "up",
+                 J: float = 1.0, sc_L: int = 0, nsites: int = 0, bond_i=None, bond_j=None, site_mask=None,
+                 bond_mask=None, stream: int | None = None):
+        st = start if isinstance(start, int) else (START_RANDOM if start == "random" else START_UP)
+        self.model = model
+        self.g = pyro_graph_init(model, seed, precision, st, J, stream, sc_L, nsites, bond_i, bond_j, site_mask,
+                                 bond_mask)
+        self.N = pyro_graph_num_sites(self.g)
+        self.NB = pyro_graph_num_bonds(self.g)
+
+    def close(self):
+        if getattr(self, "g", None):
+            pyro_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, beta: float, n: int = 1):
+        pyro_graph_sweep(self.g, beta, n)
+
+    def measure(self):
+        return pyro_graph_measure(self.g)
+
+    def stats(self):
+        return pyro_graph_stats(self.g)
+
+    def reset_stats(self):
+        pyro_graph_reset_stats(self.g)
+
+    def spins(self):
+        return pyro_graph_get_spins(self.g, self.model)
+
+    def set_spins(self, s):
+        pyro_graph_set_spins(self.g, s, self.model)
+
+    def labels(self):
+        return pyro_graph_get_labels(self.g)
+
+    @property
+    def sweep_count(self):
+        return pyro_graph_get_sweep(self.g)
+
+    @sweep_count.setter
+    def sweep_count(self, s):
+        pyro_graph_set_sweep(self.g, s)
+
+    def sync(self):
+        pyro_graph_sync(self.g)
+
+    @property
+    def stream(self):
+        return pyro_graph_get_stream(self.g)
+
+    @property
+    def launches(self):
+        return pyro_graph_launch_count(self.g)

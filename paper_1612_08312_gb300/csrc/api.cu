@@ -191,6 +191,7 @@ static int measure_of(Engine &e, int r, double *E, double *m2, double *m4)
 cudaError_t ising_set_unite_bound(int bound);
 int noalloc_set_stamp(uint32_t stamp);
 cudaError_t vec_set_unite_bound(int bound);
+cudaError_t graph_set_unite_bound(int bound);
 
 // ------------------------------------------------------------- autotuner --
 // Candidate tiles: powers of two, 64 to 512 cells, each edge dividing L
@@ -619,6 +620,7 @@ int pyro_debug_set(int key, int64_t value)
         const int b = value <= 0 ? 0 : (value > 4096 ? 4096 : (int)value);
         PYRO_CUDA(ising_set_unite_bound(b), "bound update");
         PYRO_CUDA(vec_set_unite_bound(b), "bound update");
+        PYRO_CUDA(graph_set_unite_bound(b), "bound update");
         return PYRO_OK;
     }
     return fail(PYRO_E_INVAL, "unknown debug key");

@@ -73,6 +73,8 @@ uint64_t ising_threshold(double beta, double J);
 // Test hooks (pyro_debug_set): the next `fail_allocs` device allocations
 // of an engine set-up report failure.
 extern int g_fail_allocs;
+// cudaMalloc behind the fail_allocs hook.
+cudaError_t engine_malloc(void **p, size_t bytes);
 // Test hook (pyro_debug_set): the crossing-link stamp that engines created
 // from now on start at (0 by default), so that a test can take a chain
 // across the stamps' wrap-around.
