@@ -7,8 +7,11 @@ Default workload: the L = 256 Ising lattice (N = 16 * 256^3 = 268,435,456
 sites) at T = 4.21394 from a Philox-random start, the workload the headline
 metric is quoted on.  --workload selects the other runs (L = 8 Ising, 48
 batched Ising replicas, XY L = 64 in FP32 with the plain FP64 form beside it,
-24 batched Heisenberg replicas likewise).  The metric is site updates per
-nanosecond (sites * steps / time).
+24 batched Heisenberg replicas likewise, one Heisenberg L = 128 lattice) and
+the generic-lattice path (the simple-cubic Ising lattice at L = 640 with
+implicit bonds, at L = 512 as an explicit bond list, and at L = 512 with 80 %
+of its sites occupied).  The metric is site updates per nanosecond
+(sites * steps / time).
 
 Multi-GPU: independent replicas, one lattice per rank with its own seed (the
 sweep of one lattice does not shard), so scaling is weak and there is no
@@ -155,7 +158,11 @@ def cpu_baseline(wl: dict, args, seconds: float = 12.0, max_sweeps: int = 40):
     import oracle
     L = 8 if args.workload == "ising_L8" else 32
     T = wl["T"]
-    o = oracle.Oracle(L, wl["model"], 1, "random")
+    if "lattice" in wl:
+        L = 80  # simple cubic: 512,000 sites, about the pyrochlore L = 32 sample's count
+        o = graph_oracle(wl, L, 1)
+    else:
+        o = oracle.Oracle(L, wl["model"], 1, "random")
     o.sweep(1.0 / T, 1)
     n, t0 = 0, time.perf_counter()
     while n < max_sweeps and time.perf_counter() - t0 < seconds:
@@ -163,7 +170,8 @@ def cpu_baseline(wl: dict, args, seconds: float = 12.0, max_sweeps: int = 40):
         n += 1
     dt = time.perf_counter() - t0
     return {"value": o.N * n / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle, model {wl['model']} L={L} (N={o.N}) at T={T}, random start, {n} timed sweeps "
+            "sample": f"oracle, model {wl['model']} {'simple cubic' if 'lattice' in wl else 'pyrochlore'} L={L} "
+                      f"(N={o.N}) at T={T}, random start, {n} timed sweeps "
                       f"after 1 untimed ({dt:.1f} s, single thread)"}
 
 
@@ -196,7 +204,11 @@ def run_reference(args, world, rank):
     wl = WORKLOADS[args.workload]
     model, T, L = wl["model"], wl["T"], args.ref_L
     import oracle
-    o = oracle.Oracle(L, model, 1, "random")
+    if "lattice" in wl:
+        L = max(L, 80)
+        o = graph_oracle(wl, L, 1)
+    else:
+        o = oracle.Oracle(L, model, 1, "random")
     for _ in range(args.warmup):
         o.sweep(1.0 / T, 1)
     t0 = time.perf_counter()
@@ -222,9 +234,45 @@ WORKLOADS = {
     "ising_batch48": dict(model=1, Ls=workloads.ISING_BATCH["L"], Ts=workloads.ISING_BATCH["T"], T=4.21394,
                           start="random", seed=1, precision=1, dtype="u8", dtype_ref="i8"),
     "xy_L64": dict(model=2, L=64, T=2.0285, start="random", seed=1, precision=0, dtype="f32", dtype_ref="f64"),
+    "heis_L128": dict(model=3, L=128, T=1.31695, start="random", seed=1, precision=0, dtype="f32", dtype_ref="f64"),
     "heis_batch24": dict(model=3, Ls=workloads.HEIS_BATCH["L"], Ts=workloads.HEIS_BATCH["T"], T=1.31695,
                          start="random", seed=1, precision=0, dtype="f32", dtype_ref="f64"),
+    # generic-lattice path (simple cubic, implicit bonds / explicit bond list / site-diluted)
+    "sc_L640": dict(model=1, lattice="sc", L=workloads.SC_L640["L"], T=workloads.SC_L640["T"], start="random",
+                    seed=1, precision=1, dtype="i8", dtype_ref="i8"),
+    "sc_dil_L512": dict(model=1, lattice="sc", L=workloads.SC_DIL_L512["L"], T=workloads.SC_DIL_L512["T"],
+                        p_site=workloads.SC_DIL_L512["p_site"], mask_seed=workloads.SC_DIL_L512["mask_seed"],
+                        start="random", seed=1, precision=1, dtype="i8", dtype_ref="i8"),
+    "sc_list_L512": dict(model=1, lattice="list", L=workloads.SC_LIST_L512["L"], T=workloads.SC_LIST_L512["T"],
+                         start="random", seed=1, precision=1, dtype="i8", dtype_ref="i8"),
 }
+
+
+def graph_bytes_per_site(wl: dict) -> float:
+    """Algorithmic bytes per site update of a generic-lattice Ising sweep:
+    the int8 spin read and written (2), the union-find array's identity
+    entry written, read once and the canonical label written (12); an
+    explicit bond list adds its two int32 endpoints per bond (3 bonds per
+    simple-cubic site: 24)."""
+    return 14.0 + (24.0 if wl["lattice"] == "list" else 0.0)
+
+
+def make_graph(pyro, wl: dict, L: int, seed: int):
+    """The generic-lattice object of a workload (simple cubic L^3)."""
+    kw = dict(sc_L=L)
+    if wl["lattice"] == "list":
+        bi, bj = workloads.sc_bond_list(L)
+        kw = dict(nsites=L ** 3, bond_i=bi, bond_j=bj)
+    if "p_site" in wl:
+        kw["site_mask"] = workloads.site_mask(L ** 3, wl["p_site"], wl["mask_seed"])
+    return pyro.Graph(wl["model"], seed, precision=wl["precision"], start=wl["start"], **kw)
+
+
+def graph_oracle(wl: dict, L: int, seed: int):
+    import oracle
+    bi, bj = oracle.sc_edges(L)
+    mask = workloads.site_mask(L ** 3, wl["p_site"], wl["mask_seed"]) if "p_site" in wl else None
+    return oracle.GraphOracle(L ** 3, bi, bj, wl["model"], seed, wl["start"], site_mask=mask)
 
 
 def time_device(stream, fn):
@@ -277,7 +325,17 @@ def main():
             dist.barrier()
 
     batched = "Ls" in wl
-    if batched:
+    graph = "lattice" in wl
+    if graph:
+        L = args.L or wl["L"]
+        beta = 1.0 / wl["T"]
+        obj = make_graph(pyro, wl, L, rank_seed(wl["seed"], rank))
+        N = obj.N
+        stream = torch.cuda.ExternalStream(obj.stream)
+        sweep = lambda n: obj.sweep(beta, n)
+        sync = obj.sync
+        tile = None
+    elif batched:
         reps = [(L, T) for L in wl["Ls"] for T in wl["Ts"]]
         Ls, betas = [r[0] for r in reps], [1.0 / r[1] for r in reps]
         btile = "auto" if args.tile == "auto" else ((0, 0, 0) if args.tile == "default" else
@@ -332,10 +390,20 @@ def main():
            "gpu_launches": launches, "clocks": clk}
     if batched:
         out["config"].update({"replicas": len(reps), "L": sorted(set(Ls)), "T": wl["Ts"], "graphs": True})
+    elif graph:
+        out["config"].update({"L": L, "T": wl["T"], "lattice": "simple cubic", "bonds": obj.NB,
+                              "bond_form": "explicit bond list" if wl["lattice"] == "list" else "implicit",
+                              "site_occupation": wl.get("p_site", 1.0)})
+        del out["config"]["tile"]
     else:
         out["config"].update({"L": L, "T": wl["T"]})
 
-    if not batched and model == 1:
+    sweep_bytes = graph_bytes_per_site(wl) if graph else SWEEP_BYTES[model][prec]
+    if graph:
+        out["roofline"] = {"bound": "hbm", "kernel": "whole sweep", "achieved": value * sweep_bytes, "peak": peak,
+                           "unit": "GB/s", "frac": value * sweep_bytes / peak, "peak_kind": peak_kind,
+                           "traffic": None, "alg_bytes_per_site": sweep_bytes}
+    elif not batched and model == 1:
         prof = pyro.pyro_profile_phases(obj.h, beta, 5)
         dominant = max(prof, key=prof.get)
         alg_bytes = PHASE_BYTES_PER_SITE[dominant] * N
@@ -350,12 +418,25 @@ def main():
                            "peak": peak, "unit": "GB/s", "frac": value * SWEEP_BYTES[model][prec] / peak,
                            "peak_kind": peak_kind, "traffic": None,
                            "alg_bytes_per_site": SWEEP_BYTES[model][prec]}
-    out["sweep_hbm_frac"] = value * SWEEP_BYTES[model][prec] / peak
+    out["sweep_hbm_frac"] = value * sweep_bytes / peak
 
     # end to end through the C ABI with host buffers (single lattices): per
     # step the state goes host -> device, one sweep runs, the state and the
     # measurement come back device -> host
-    if not batched:
+    if graph:
+        host = obj.spins()
+        sync()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            obj.set_spins(host)
+            sweep(1)
+            host = obj.spins()
+            obj.measure()
+        e2e_s = reduce_max(time.perf_counter() - t0, world, device="cuda")
+        out["e2e"] = {"value": N * args.e2e_steps * world / (e2e_s * 1e9), "unit": UNIT,
+                      "h2d_bytes_per_step": N, "d2h_bytes_per_step": N + 24, "steps": args.e2e_steps}
+    elif not batched:
         nbytes = pyro.pyro_state_bytes(obj.h)
         host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
         host_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)

@@ -54,18 +54,32 @@ struct GraphDev {
 
 constexpr int GB_THREADS = 256;
 
+// Simple cubic: coordinates of site s and its neighbour one step along
+// +axis d (32-bit arithmetic: N < 2^31).
+__device__ __forceinline__ void sc_coords(int L, int s, int &x, int &y, int &z)
+{
+    const unsigned us = (unsigned)s, uL = (unsigned)L, t = us / uL;
+    x = (int)(us - t * uL);
+    z = (int)(t / uL);
+    y = (int)(t - (unsigned)z * uL);
+}
+
+__device__ __forceinline__ int sc_next(int L, int s, int x, int y, int z, int d)
+{
+    if (d == 0) return x + 1 == L ? s - x : s + 1;
+    if (d == 1) return y + 1 == L ? s - y * L : s + L;
+    return z + 1 == L ? s - z * L * L : s + L * L;
+}
+
 // Sites joined by bond e.
 __device__ __forceinline__ void bond_ends(const GraphDev &G, int64_t e, int &i, int &j)
 {
     if (G.L) {
-        const int64_t L = G.L;
         const int64_t s = e / 3;
-        const int d = (int)(e - 3 * s);
-        const int64_t x = s % L, yz = s / L, y = yz % L, z = yz / L;
+        int x, y, z;
+        sc_coords(G.L, (int)s, x, y, z);
         i = (int)s;
-        if (d == 0) j = (int)(x + 1 == L ? s - x : s + 1);
-        else if (d == 1) j = (int)(y + 1 == L ? s - y * L : s + L);
-        else j = (int)(z + 1 == L ? s - z * L * L : s + L * L);
+        j = sc_next(G.L, i, x, y, z, (int)(e - 3 * s));
     } else {
         i = G.bi[e];
         j = G.bj[e];
@@ -153,6 +167,10 @@ __global__ void __launch_bounds__(GB_THREADS) graph_proj_kernel(const __grid_con
         proj[i] = project<NC, T>(sp, G.N, i, r);
 }
 
+// Thread c takes the 16 bonds 16 c .. 16 c + 15 (one BOND call) and draws
+// the FLIP call c.  (One bond per lane with the words passed by shuffles was
+// measured slower: a warp's lanes then unite the bonds of the same few sites
+// at once.)
 template <int NC, typename T>
 __global__ void __launch_bounds__(GB_THREADS) graph_bond_kernel(const __grid_constant__ GraphDev G)
 {
@@ -166,22 +184,47 @@ __global__ void __launch_bounds__(GB_THREADS) graph_bond_kernel(const __grid_con
     uint32_t pres = 0xFFFFu;
     if (G.present) pres = (G.present[e0 >> 5] >> (e0 & 31)) & 0xFFFFu;
     bool ok = true;
+    // simple cubic: bond 3 s + d, walked incrementally from the chunk's first
+    int s = 0, d = 0, x = 0, y = 0, z = 0;
+    if (G.L) {
+        const uint64_t s0 = (uint64_t)e0 / 3u;
+        s = (int)s0;
+        d = (int)((uint64_t)e0 - 3u * s0);
+        sc_coords(G.L, s, x, y, z);
+    }
 #pragma unroll 1
     for (int q = 0; q < nq; ++q) {
+        if (G.L && q > 0 && ++d == 3) {
+            d = 0;
+            ++s;
+            if (++x == G.L) {
+                x = 0;
+                if (++y == G.L) {
+                    y = 0;
+                    ++z;
+                }
+            }
+        }
         if (!((pres >> q) & 1u)) continue;
         const int64_t e = e0 + q;
         int i, j;
-        bond_ends(G, e, i, j);
+        if (G.L) {
+            i = s;
+            j = sc_next(G.L, s, x, y, z, d);
+        } else {
+            i = G.bi[e];
+            j = G.bj[e];
+        }
         uint64_t thr;
         if (NC == 1) {
-            const int8_t *s = static_cast<const int8_t *>(G.spins);
-            if (s[i] != s[j]) continue;
+            const int8_t *sp = static_cast<const int8_t *>(G.spins);
+            if (sp[i] != sp[j]) continue;
             thr = G.thr;
         } else {
             const T *p = static_cast<const T *>(G.proj);
-            const T x = Ar<T>::mul(p[i], p[j]);
-            if (!(x > (T)0)) continue;
-            thr = prob_threshold(Ar<T>::bond_p((T)G.K2, x));
+            const T xp = Ar<T>::mul(p[i], p[j]);
+            if (!(xp > (T)0)) continue;
+            thr = prob_threshold(Ar<T>::bond_p((T)G.K2, xp));
         }
         const uint64_t byte = (word_of(w, q >> 2) >> (8 * (q & 3))) & 0xFFu;
         const uint64_t hi = thr >> 24;
@@ -251,11 +294,21 @@ __global__ void __launch_bounds__(GB_THREADS) graph_measure_kernel(const __grid_
         long long e = 0, m = 0;
         for (int64_t i = t0; i < G.N; i += stride)
             if (!G.occ || bit_of(G.occ, i)) m += s[i];
-        for (int64_t b = t0; b < G.NB; b += stride) {
-            if (G.present && !bit_of(G.present, b)) continue;
-            int i, j;
-            bond_ends(G, b, i, j);
-            e += s[i] == s[j] ? 1 : -1;
+        if (G.L) {
+            for (int64_t i = t0; i < G.N; i += stride) {
+                int x, y, z;
+                sc_coords(G.L, (int)i, x, y, z);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (G.present && !bit_of(G.present, 3 * i + d)) continue;
+                    e += s[i] == s[sc_next(G.L, (int)i, x, y, z, d)] ? 1 : -1;
+                }
+            }
+        } else {
+            for (int64_t b = t0; b < G.NB; b += stride) {
+                if (G.present && !bit_of(G.present, b)) continue;
+                e += s[G.bi[b]] == s[G.bj[b]] ? 1 : -1;
+            }
         }
         v[0] = (double)e;
         v[1] = (double)m;

@@ -292,10 +292,8 @@ size_t resolve_smem(const TileShape &t) { return resolve_smem_bytes(t.TX * t.TY 
 
 cudaError_t ising_prepare(const TileShape &t)
 {
-    const int mx = smem_optin();
-    if ((int)ising_local_smem(t) > mx || (int)resolve_smem(t) > mx) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(ising_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(ising_flip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaError_t e = allow_dynamic_smem(ising_local_kernel, ising_local_smem(t));
+    if (e == cudaSuccess) e = allow_dynamic_smem(ising_flip_kernel, resolve_smem(t));
     return e;
 }
 

@@ -178,4 +178,18 @@ inline int smem_optin()
     return v;
 }
 
+// Let kernel k take up to `need` bytes of dynamic shared memory: invalid if
+// that and its static shared memory exceed the opt-in limit, else the
+// attribute is raised to what the static part leaves.
+template <typename K>
+inline cudaError_t allow_dynamic_smem(K k, size_t need)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k);
+    if (e != cudaSuccess) return e;
+    const int room = smem_optin() - (int)a.sharedSizeBytes;
+    if ((int)need > room) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
+}
+
 }  // namespace pyro

@@ -39,9 +39,12 @@ __global__ void __launch_bounds__(512) vec_local_kernel(const __grid_constant__ 
     const uint64_t seed = R.seed;
     core_prologue(sm);
 
-    double rd[3];
-    unit_vector_dev<NC>(seed, sweep, TAG_AXIS, 0, rd);
-    const T r[3] = {(T)rd[0], (T)rd[1], (T)rd[2]};
+    // the sweep's axis, drawn once per block (FP64 divides and square roots
+    // run at a small fraction of the FP32 rate on this GPU)
+    __shared__ double s_axis[3];
+    if (threadIdx.x == 0) unit_vector_dev<NC>(seed, sweep, TAG_AXIS, 0, s_axis);
+    __syncthreads();
+    const T r[3] = {(T)s_axis[0], (T)s_axis[1], (T)s_axis[2]};
 
     // projections s_i . r of the tile's sites and the backward halo
     const int nh = halo_cells(c.TX, c.TY, c.TZ);
@@ -103,11 +106,11 @@ __global__ void __launch_bounds__(512) vec_flip_kernel(const __grid_constant__ B
     const int rep = find_rep(B.tile_begin, B.R, blockIdx.x);
     const Rep &R = B.reps[rep];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[rep]);
-    uint32_t flip = cell_flip_mask(c, R, smem);
+    __shared__ double s_axis[3];
+    if (threadIdx.x == 0) unit_vector_dev<NC>(R.seed, (uint32_t)R.st->sweep, TAG_AXIS, 0, s_axis);
+    uint32_t flip = cell_flip_mask(c, R, smem);  // its barrier also publishes s_axis
     if (!flip) return;
-    double rd[3];
-    unit_vector_dev<NC>(R.seed, (uint32_t)R.st->sweep, TAG_AXIS, 0, rd);
-    const T r[3] = {(T)rd[0], (T)rd[1], (T)rd[2]};
+    const T r[3] = {(T)s_axis[0], (T)s_axis[1], (T)s_axis[2]};
     T *spins = static_cast<T *>(R.spins);
     const int64_t N = R.N;
     while (flip) {
@@ -129,7 +132,9 @@ __global__ void __launch_bounds__(512) vec_flip_kernel(const __grid_constant__ B
 }
 
 // Energy (Eq. 1) and magnetisation of the current configuration: every
-// cell sums the 48 bonds it owns and its 16 spins in FP64; one partial
+// cell sums the 48 bonds it owns and its 16 spins (FP64 spins in FP64; FP32
+// spins in FP32 within the cell, since FP64 adds and conversions run at a
+// small fraction of the FP32 rate on this GPU), then in FP64; one partial
 // (E, M_x, M_y, M_z) per tile, summed in a fixed order.
 template <int NC, typename T>
 __global__ void __launch_bounds__(512) vec_measure_kernel(const __grid_constant__ Batch B)
@@ -151,11 +156,12 @@ __global__ void __launch_bounds__(512) vec_measure_kernel(const __grid_constant_
         const int cz = (m & 4) ? wrap_back(z, L) : z;
         cb[m] = 16 * ((int64_t)cx + (int64_t)L * ((int64_t)cy + (int64_t)L * cz));
     }
-    double e = 0.0, M[3] = {0.0, 0.0, 0.0};
+    using Acc = T;  // the cell's own sums: the spins' precision
+    Acc ec = (Acc)0, Mc[3] = {(Acc)0, (Acc)0, (Acc)0};
 #pragma unroll
     for (int s = 0; s < 16; ++s)
 #pragma unroll
-        for (int k = 0; k < NC; ++k) M[k] += (double)sp[k * N + cb[0] + s];
+        for (int k = 0; k < NC; ++k) Mc[k] += (Acc)sp[k * N + cb[0] + s];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
 #pragma unroll
@@ -170,9 +176,10 @@ __global__ void __launch_bounds__(512) vec_measure_kernel(const __grid_constant_
             T dd = sp[id] * sp[jd];
 #pragma unroll
             for (int q = 1; q < NC; ++q) dd += sp[q * N + id] * sp[q * N + jd];
-            e += (double)du + (double)dd;
+            ec += du + dd;
         }
     }
+    const double e = (double)ec, M[3] = {(double)Mc[0], (double)Mc[1], (double)Mc[2]};
     const double se = tile_sum_f64(e, c.nt, scratch);
     const double s0 = tile_sum_f64(M[0], c.nt, scratch);
     const double s1 = tile_sum_f64(M[1], c.nt, scratch);
@@ -223,10 +230,8 @@ template <int NC, typename T>
 struct VecOps {
     static cudaError_t prepare(const TileShape &t, int prec)
     {
-        const int mx = smem_optin();
-        if ((int)vec_local_smem(t, prec) > mx || (int)resolve_smem(t) > mx) return cudaErrorInvalidValue;
-        cudaError_t e = cudaFuncSetAttribute(vec_local_kernel<NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(vec_flip_kernel<NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaError_t e = allow_dynamic_smem(vec_local_kernel<NC, T>, vec_local_smem(t, prec));
+        if (e == cudaSuccess) e = allow_dynamic_smem(vec_flip_kernel<NC, T>, resolve_smem(t));
         return e;
     }
     static void init(const Batch &B, int64_t nblocks, int random, cudaStream_t s)
