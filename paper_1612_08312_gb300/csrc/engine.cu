@@ -473,7 +473,7 @@ cudaError_t Engine::profile(int n, double *phase_ms)
             enqueue_phase(p, 1);
             cudaEventRecord(ev[p + 1], stream);
         }
-        launches += NPHASE;
+        launches += launches_per_sweep();
         e = cudaEventSynchronize(ev[NPHASE]);
         for (int p = 0; p < NPHASE && e == cudaSuccess; ++p) {
             float ms = 0.f;
@@ -488,7 +488,9 @@ cudaError_t Engine::profile(int n, double *phase_ms)
     return e;
 }
 
-int Engine::launches_per_sweep() const { return NPHASE; }
+// Kernel launches of one sweep: one per phase, and the crossing phase is
+// two (unions, then the roots' correction bits).
+int Engine::launches_per_sweep() const { return NPHASE + 1; }
 
 cudaGraphExec_t Engine::graph_for(int n)
 {

@@ -10,8 +10,8 @@ namespace pyro {
 
 // Sweeps captured per CUDA graph for long runs.
 constexpr int GRAPH_CHUNK = 32;
-// Kernel launches (phases) per sweep: tile-local labelling, crossing
-// unions, flip, measurement, accumulation.
+// Phases of a sweep: tile-local labelling, crossing unions (two launches),
+// flip, measurement, accumulation.
 constexpr int NPHASE = 5;
 
 struct GraphEntry {

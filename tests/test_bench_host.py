@@ -33,6 +33,10 @@ def test_fingerprint_ignores_comments_and_whitespace_but_not_code(tmp_path):
     assert fingerprint(root) == base
     f.write_text(text.replace("MEASURE_BLOCK = 128", "MEASURE_BLOCK = 64"))
     assert fingerprint(root) != base
+    f.write_text(text)
+    g = root / "paper_1612_08312_gb300" / "csrc" / "graph.cu"
+    g.write_text(g.read_text().replace("GB_THREADS = 256", "GB_THREADS = 128"))
+    assert fingerprint(root) == base  # another model's kernels
 
 
 def test_committed_traffic_is_read_per_kernel_and_fingerprint(tmp_path):

@@ -42,7 +42,9 @@ def test_batch_graph_chunks_and_launch_accounting():
     l0 = b.launches
     b.sweep(70)  # two 32-sweep graphs plus six single-sweep graphs
     b.sync()
-    assert b.launches - l0 == 70 * 5
+    # per sweep: local labelling, crossing unions, crossing roots, flip,
+    # measurement, accumulation
+    assert b.launches - l0 == 70 * 6
     s = b.stats(0)
     assert s["count"] == 70
 
