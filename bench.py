@@ -154,7 +154,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(wl: dict, args, seconds: float = 12.0, max_sweeps: int = 40):
+def cpu_baseline(wl: dict, args, seconds: float = 12.0, max_sweeps: int = 400):
     """Time the oracle (single-threaded C) on a bounded sample of the
     workload: one L = 32 lattice of the workload's model and temperature
     (L = 8 for the L = 8 workload) from the random start."""
@@ -427,15 +427,19 @@ def main():
     # step the state goes host -> device, one sweep runs, the state and the
     # measurement come back device -> host
     if graph:
-        host = obj.spins()
+        # pinned host buffers (int8 spins in site order)
+        host_in = torch.empty(N, dtype=torch.int8, pin_memory=True).numpy()
+        host_out = torch.empty(N, dtype=torch.int8, pin_memory=True).numpy()
+        obj.spins(out=host_in)
         sync()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            obj.set_spins(host)
+            obj.set_spins(host_in)
             sweep(1)
-            host = obj.spins()
+            obj.spins(out=host_out)
             obj.measure()
+            host_in, host_out = host_out, host_in
         e2e_s = reduce_max(time.perf_counter() - t0, world, device="cuda")
         out["e2e"] = {"value": N * args.e2e_steps * world / (e2e_s * 1e9), "unit": UNIT,
                       "h2d_bytes_per_step": N, "d2h_bytes_per_step": N + 24, "steps": args.e2e_steps}

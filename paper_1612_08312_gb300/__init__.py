@@ -500,9 +500,13 @@ def pyro_graph_num_bonds(g) -> int:
     return int(lib().pyro_graph_num_bonds(g))
 
 
-def pyro_graph_get_spins(g, model: int) -> np.ndarray:
+def pyro_graph_get_spins(g, model: int, out: np.ndarray | None = None) -> np.ndarray:
+    """Spins in site order (Ising int8, n-vector float64 N x n); `out`, if
+    given, is a C-contiguous array of that shape and type to fill (for
+    instance a view of pinned host memory)."""
     N = pyro_graph_num_sites(g)
-    out = np.zeros(N, dtype=np.int8) if model == ISING else np.zeros((N, model), dtype=np.float64)
+    if out is None:
+        out = np.zeros(N, dtype=np.int8) if model == ISING else np.zeros((N, model), dtype=np.float64)
     _check(lib().pyro_graph_get_spins(g, _buf(out), out.nbytes))
     return out
 
@@ -716,8 +720,8 @@ class Graph:
     def reset_stats(self):
         pyro_graph_reset_stats(self.g)
 
-    def spins(self):
-        return pyro_graph_get_spins(self.g, self.model)
+    def spins(self, out=None):
+        return pyro_graph_get_spins(self.g, self.model, out)
 
     def set_spins(self, s):
         pyro_graph_set_spins(self.g, s, self.model)
