@@ -87,8 +87,10 @@ __device__ __forceinline__ uint64_t prob_threshold(double p)
 __device__ __forceinline__ uint64_t prob_threshold(float p)
 {
     if (!(p > 0.0f)) return 0;
-    const float t = floorf(p * 4294967296.0f);
-    return t >= 4294967296.0f ? (1ull << 32) : (uint64_t)__float2ull_rz(t);
+    if (p >= 1.0f) return 1ull << 32;
+    // p < 1: p 2^32 (exact, a power-of-two scaling) is below 2^32, and the
+    // truncating conversion is the floor
+    return __float2uint_rz(p * 4294967296.0f);
 }
 
 }  // namespace pyro

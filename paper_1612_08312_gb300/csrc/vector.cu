@@ -23,8 +23,33 @@
 
 namespace pyro {
 
+// 16 consecutive values of T (a cell's sites of one component, 64- or
+// 128-byte aligned) to and from registers in 16-byte accesses.
+template <typename T>
+__device__ __forceinline__ void load16(const T *p, T out[16])
+{
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(T)); ++k) {
+        const uint4 w = q[k];
+        memcpy(&out[k * 16 / (int)sizeof(T)], &w, 16);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store16(T *p, const T in[16])
+{
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(T)); ++k) {
+        uint4 w;
+        memcpy(&w, &in[k * 16 / (int)sizeof(T)], 16);
+        q[k] = w;
+    }
+}
+
 template <int NC, typename T>
-__global__ void __launch_bounds__(512) vec_local_kernel(const __grid_constant__ Batch B)
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) vec_local_kernel(const __grid_constant__ Batch B)
 {
     using A = Ar<T>;
     extern __shared__ __align__(16) int smem[];
@@ -46,12 +71,16 @@ __global__ void __launch_bounds__(512) vec_local_kernel(const __grid_constant__ 
     __syncthreads();
     const T r[3] = {(T)s_axis[0], (T)s_axis[1], (T)s_axis[2]};
 
-    // projections s_i . r of the tile's sites and the backward halo
+    // projections s_i . r of the tile's sites and the backward halo; each
+    // halo cell's first site is found once (the halo's edges are not powers
+    // of two, so this takes divisions) and shared
     const int nh = halo_cells(c.TX, c.TY, c.TZ);
-    for (int idx = threadIdx.x; idx < 16 * nh; idx += blockDim.x) {
-        const int64_t i = 16 * halo_cell(idx >> 4, c.TX, c.TY, c.ox, c.oy, c.oz, c.L) + (idx & 15);
-        proj[idx] = project<NC, T>(spins, N, i, r);
-    }
+    int *hbase = reinterpret_cast<int *>(proj + 16 * nh);
+    for (int h = threadIdx.x; h < nh; h += blockDim.x)
+        hbase[h] = (int)(16 * halo_cell(h, c.TX, c.TY, c.ox, c.oy, c.oz, c.L));
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 16 * nh; idx += blockDim.x)
+        proj[idx] = project<NC, T>(spins, N, (int64_t)hbase[idx >> 4] + (idx & 15), r);
     __syncthreads();
 
     const T K2 = (T)R.K2;
@@ -113,22 +142,50 @@ __global__ void __launch_bounds__(512) vec_flip_kernel(const __grid_constant__ B
     const T r[3] = {(T)s_axis[0], (T)s_axis[1], (T)s_axis[2]};
     T *spins = static_cast<T *>(R.spins);
     const int64_t N = R.N;
-    while (flip) {
-        const int s = __ffs(flip) - 1;
-        flip &= flip - 1;
-        const int64_t i = 16 * c.cell + s;
-        const T pr = project<NC, T>(spins, N, i, r);
+    if (NC * sizeof(T) > 16) {
+        // FP64 Heisenberg: a cell's 48 doubles do not fit the registers;
+        // site by site
+        while (flip) {
+            const int s = __ffs(flip) - 1;
+            flip &= flip - 1;
+            const int64_t i = 16 * c.cell + s;
+            const T pr = project<NC, T>(spins, N, i, r);
+            const T d2 = A::mul((T)2, pr);
+            T t[3];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) t[k] = A::sub(spins[k * N + i], A::mul(d2, r[k]));
+            T q = A::mul(t[0], t[0]);
+#pragma unroll
+            for (int k = 1; k < NC; ++k) q = A::add(q, A::mul(t[k], t[k]));
+            q = A::sqrt_(q);
+#pragma unroll
+            for (int k = 0; k < NC; ++k) spins[k * N + i] = A::div(t[k], q);
+        }
+        return;
+    }
+    // the cell's 16 sites of every component in registers (16-byte loads)
+    T sv[NC][16];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) load16(spins + k * N + 16 * c.cell, sv[k]);
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        if (!((flip >> s) & 1u)) continue;
+        T pr = A::mul(sv[0][s], r[0]);  // the projection, in the order of project()
+#pragma unroll
+        for (int k = 1; k < NC; ++k) pr = A::add(pr, A::mul(sv[k][s], r[k]));
         const T d2 = A::mul((T)2, pr);
-        T sv[3];
+        T t[3];
 #pragma unroll
-        for (int k = 0; k < NC; ++k) sv[k] = A::sub(spins[k * N + i], A::mul(d2, r[k]));
-        T q = A::mul(sv[0], sv[0]);
+        for (int k = 0; k < NC; ++k) t[k] = A::sub(sv[k][s], A::mul(d2, r[k]));
+        T q = A::mul(t[0], t[0]);
 #pragma unroll
-        for (int k = 1; k < NC; ++k) q = A::add(q, A::mul(sv[k], sv[k]));
+        for (int k = 1; k < NC; ++k) q = A::add(q, A::mul(t[k], t[k]));
         q = A::sqrt_(q);
 #pragma unroll
-        for (int k = 0; k < NC; ++k) spins[k * N + i] = A::div(sv[k], q);
+        for (int k = 0; k < NC; ++k) sv[k][s] = A::div(t[k], q);
     }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) store16(spins + k * N + 16 * c.cell, sv[k]);
 }
 
 // Energy (Eq. 1) and magnetisation of the current configuration: every
@@ -156,26 +213,36 @@ __global__ void __launch_bounds__(512) vec_measure_kernel(const __grid_constant_
         const int cz = (m & 4) ? wrap_back(z, L) : z;
         cb[m] = 16 * ((int64_t)cx + (int64_t)L * ((int64_t)cy + (int64_t)L * cz));
     }
+    // the cell's own 16 sites in registers (16-byte loads); the down
+    // tetrahedra's vertices in backward cells are read from global memory
+    T sv[NC][16];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) load16(sp + k * N + cb[0], sv[k]);
     using Acc = T;  // the cell's own sums: the spins' precision
     Acc ec = (Acc)0, Mc[3] = {(Acc)0, (Acc)0, (Acc)0};
 #pragma unroll
     for (int s = 0; s < 16; ++s)
 #pragma unroll
-        for (int k = 0; k < NC; ++k) Mc[k] += (Acc)sp[k * N + cb[0] + s];
+        for (int k = 0; k < NC; ++k) Mc[k] += (Acc)sv[k][s];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int va = pair_a(k), vb = pair_b(k);
-            const int64_t iu = cb[0] + 4 * f + va, ju = cb[0] + 4 * f + vb;
-            T du = sp[iu] * sp[ju];
+            T du = sv[0][4 * f + va] * sv[0][4 * f + vb];
 #pragma unroll
-            for (int q = 1; q < NC; ++q) du += sp[q * N + iu] * sp[q * N + ju];
-            const int64_t id = cb[down_mask(f, va)] + down_bit(f, va);
-            const int64_t jd = cb[down_mask(f, vb)] + down_bit(f, vb);
-            T dd = sp[id] * sp[jd];
+            for (int q = 1; q < NC; ++q) du += sv[q][4 * f + va] * sv[q][4 * f + vb];
+            const int ma = down_mask(f, va), mb = down_mask(f, vb);
+            const int ba = down_bit(f, va), bb = down_bit(f, vb);
+            T xa[3], xb[3];
 #pragma unroll
-            for (int q = 1; q < NC; ++q) dd += sp[q * N + id] * sp[q * N + jd];
+            for (int q = 0; q < NC; ++q) {
+                xa[q] = ma == 0 ? sv[q][ba] : sp[q * N + cb[ma] + ba];
+                xb[q] = mb == 0 ? sv[q][bb] : sp[q * N + cb[mb] + bb];
+            }
+            T dd = xa[0] * xb[0];
+#pragma unroll
+            for (int q = 1; q < NC; ++q) dd += xa[q] * xb[q];
             ec += du + dd;
         }
     }
@@ -221,7 +288,9 @@ void launch_boundary(const Batch &B, int64_t ntiles, cudaStream_t s);
 size_t vec_local_smem(const TileShape &t, int prec)
 {
     const size_t es = prec == PYRO_FP64 ? 8 : 4;
-    return core_smem_bytes(t.TX * t.TY * t.TZ) + (size_t)16 * halo_cells(t.TX, t.TY, t.TZ) * es;
+    // core area, the halo's projections, the halo cells' first sites
+    return core_smem_bytes(t.TX * t.TY * t.TZ) + (size_t)16 * halo_cells(t.TX, t.TY, t.TZ) * es +
+           (size_t)halo_cells(t.TX, t.TY, t.TZ) * 4;
 }
 
 static size_t vec_measure_smem(const TileShape &t) { return (size_t)t.TX * t.TY * t.TZ * sizeof(double); }
