@@ -122,12 +122,33 @@ def test_vector_sweep_recomputed(model, L, T):
         assert np.allclose(np.linalg.norm(o.spins(), axis=1), 1, atol=1e-14)
 
 
+# The documented (g, q) -> (tetrahedron, vertex pair) table of the bond ids
+# (include/pyro.h), written out here from that text.
+DOC_ID_TABLE = {(0, 0): ("up", (0, 1)), (0, 1): ("up", (1, 2)), (0, 2): ("up", (2, 3)), (0, 3): ("up", (0, 3)),
+                (1, 0): ("up", (0, 2)), (1, 1): ("up", (1, 3)), (1, 2): ("down", (0, 2)), (1, 3): ("down", (1, 3)),
+                (2, 0): ("down", (0, 1)), (2, 1): ("down", (1, 2)), (2, 2): ("down", (2, 3)), (2, 3): ("down", (0, 3))}
+
+
 def test_bond_rng_ids_are_a_permutation():
     # every cell's 48 bonds use 48 distinct ids 48 c .. 48 c + 47
     o = oracle.Oracle(2, oracle.ISING, 1)
     ids = np.array([oracle.bond_rng_id(b) for b in range(3 * o.N)])
     assert (np.sort(ids) == np.arange(3 * o.N)).all()
-    assert (ids == refmath.bond_rng_ids(3 * o.N)).all()
+    # and each id 48 c + 16 g + 4 f + q names the bond the documentation
+    # says: the oracle's own bond list gives each bond's cell, FCC point,
+    # tetrahedron (both ends among sites 4r .. 4r + 3: up) and vertex pair
+    # (the ends' basis indices)
+    bi, bj = o.bonds()
+    for b in range(3 * o.N):
+        r = b // 12
+        i, j = int(bi[b]), int(bj[b])
+        tet = "up" if i >> 2 == r and j >> 2 == r else "down"
+        pair = tuple(sorted((i & 3, j & 3)))
+        c, rest = divmod(int(ids[b]), 48)
+        g, fq = divmod(rest, 16)
+        f, q = divmod(fq, 4)
+        assert c == r >> 2 and f == (r & 3), b
+        assert DOC_ID_TABLE[(g, q)] == (tet, pair), b
 
 
 def test_clusters_match_scipy_on_random_graphs():
