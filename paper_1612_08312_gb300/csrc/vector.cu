@@ -73,14 +73,17 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) vec_local_kernel(
 
     // projections s_i . r of the tile's sites and the backward halo; each
     // halo cell's first site is found once (the halo's edges are not powers
-    // of two, so this takes divisions) and shared
+    // of two, so this takes divisions) and shared.  Site-major layout (site s
+    // of halo cell h at s nh + h): a warp's consecutive cells read
+    // consecutive words (nh is odd, so the staging writes of one cell's 16
+    // sites fall in 16 different banks too)
     const int nh = halo_cells(c.TX, c.TY, c.TZ);
     int *hbase = reinterpret_cast<int *>(proj + 16 * nh);
     for (int h = threadIdx.x; h < nh; h += blockDim.x)
         hbase[h] = (int)(16 * halo_cell(h, c.TX, c.TY, c.ox, c.oy, c.oz, c.L));
     __syncthreads();
     for (int idx = threadIdx.x; idx < 16 * nh; idx += blockDim.x)
-        proj[idx] = project<NC, T>(spins, N, (int64_t)hbase[idx >> 4] + (idx & 15), r);
+        proj[(idx & 15) * nh + (idx >> 4)] = project<NC, T>(spins, N, (int64_t)hbase[idx >> 4] + (idx & 15), r);
     __syncthreads();
 
     const T K2 = (T)R.K2;
@@ -97,11 +100,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) vec_local_kernel(
                     const int va = slot_a(g, q), vb = slot_b(g, q);
                     T pa, pb;
                     if (slot_up(g, q)) {
-                        pa = proj[16 * halo_index(c, 0) + 4 * f + va];
-                        pb = proj[16 * halo_index(c, 0) + 4 * f + vb];
+                        pa = proj[(4 * f + va) * nh + halo_index(c, 0)];
+                        pb = proj[(4 * f + vb) * nh + halo_index(c, 0)];
                     } else {
-                        pa = proj[16 * halo_index(c, down_mask(f, va)) + down_bit(f, va)];
-                        pb = proj[16 * halo_index(c, down_mask(f, vb)) + down_bit(f, vb)];
+                        pa = proj[down_bit(f, va) * nh + halo_index(c, down_mask(f, va))];
+                        pb = proj[down_bit(f, vb) * nh + halo_index(c, down_mask(f, vb))];
                     }
                     xb[4 * f + q] = A::mul(pa, pb);
                     pos |= (xb[4 * f + q] > (T)0 ? 1u : 0u) << (4 * f + q);
