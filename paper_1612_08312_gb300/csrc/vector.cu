@@ -118,8 +118,24 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) vec_local_kernel(
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (!((pos >> (4 * f + q)) & 1u)) continue;
-                    const ByteCompare bc(prob_threshold(A::bond_p(K2, xb[4 * f + q])));
                     const uint32_t byte = (ww[f] >> (8 * q)) & 0xFFu;
+                    if (sizeof(T) == 4) {
+                        // FP32: p = 1 - exp(-y), y = K2 x, exceeds (b + 1) / 256 (so the
+                        // bond is on whatever the low bits) when y > -ln(1 - (b + 1) / 256),
+                        // and stays below b / 256 (off) when y < -ln(1 - b / 256); the
+                        // margins (1e-4 relative, 1e-6 absolute) exceed the errors of
+                        // expm1f (1 ulp of p) and of __logf, so only bonds within them
+                        // take the exact path below, with the same decision either way
+                        const float y = (float)K2 * (float)xb[4 * f + q];
+                        const float ylo = -__logf(1.0f - (float)byte * (1.0f / 256.0f));
+                        const float yhi = -__logf(1.0f - (float)(byte + 1) * (1.0f / 256.0f));  // +inf for 255
+                        if (y > yhi * 1.0001f + 1e-6f) {
+                            a |= 1u << (4 * f + q);
+                            continue;
+                        }
+                        if (y < ylo * 0.9999f - 1e-6f) continue;
+                    }
+                    const ByteCompare bc(prob_threshold(A::bond_p(K2, xb[4 * f + q])));
                     bool on = bc.all || byte < bc.t8;
                     if (!bc.all && !bc.none && byte == bc.t8) on = tie_bits(seed, sweep, c.cell, g, f, q) < bc.t24;
                     a |= (on && !bc.none ? 1u : 0u) << (4 * f + q);
