@@ -36,6 +36,18 @@ __device__ __forceinline__ void load16(const T *p, T out[16])
     }
 }
 
+// 4 consecutive values of T (16-byte aligned) in 16-byte accesses.
+template <typename T>
+__device__ __forceinline__ void load4(const T *p, T out[4])
+{
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(T)) / 4; ++k) {
+        const uint4 w = q[k];
+        memcpy(&out[k * 16 / (int)sizeof(T)], &w, 16);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void store16(T *p, const T in[16])
 {
@@ -82,8 +94,22 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) vec_local_kernel(
     for (int h = threadIdx.x; h < nh; h += blockDim.x)
         hbase[h] = (int)(16 * halo_cell(h, c.TX, c.TY, c.ox, c.oy, c.oz, c.L));
     __syncthreads();
-    for (int idx = threadIdx.x; idx < 16 * nh; idx += blockDim.x)
-        proj[(idx & 15) * nh + (idx >> 4)] = project<NC, T>(spins, N, (int64_t)hbase[idx >> 4] + (idx & 15), r);
+    // four consecutive sites per thread, each component read in 16-byte
+    // accesses (a cell's sites are 16-byte aligned in every plane)
+    for (int idx = threadIdx.x; idx < 4 * nh; idx += blockDim.x) {
+        const int h = idx >> 2, s0 = 4 * (idx & 3);
+        const int64_t i0 = (int64_t)hbase[h] + s0;
+        T v[NC][4];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) load4(spins + k * N + i0, v[k]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T pr = A::mul(v[0][q], r[0]);  // in the order of project()
+#pragma unroll
+            for (int k = 1; k < NC; ++k) pr = A::add(pr, A::mul(v[k][q], r[k]));
+            proj[(s0 + q) * nh + h] = pr;
+        }
+    }
     __syncthreads();
 
     const T K2 = (T)R.K2;
