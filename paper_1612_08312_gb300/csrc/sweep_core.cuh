@@ -71,22 +71,27 @@ __device__ __forceinline__ unsigned lanes_mask(int nt)
     return cnt >= 32 ? 0xffffffffu : ((1u << cnt) - 1u);
 }
 
-// Deterministic sum over the block's nt threads (fixed tree in shared
-// memory, any nt); result valid in thread 0.  scratch holds nt doubles.
-__device__ __forceinline__ double tile_sum_f64(double v, int nt, double *scratch)
+// Deterministic sums of four doubles over the block's nt threads: a fixed
+// tree in shared memory (any nt), one barrier per level for all four;
+// results valid in thread 0.  scratch holds 4 nt doubles.  (A warp-shuffle
+// tree would add in FP64 on every lane at every level; FP64 adds are scarce
+// on this GPU.)
+__device__ __forceinline__ void tile_sum4_f64(double v[4], int nt, double *scratch)
 {
     const int t = threadIdx.x;
-    scratch[t] = v;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) scratch[q * nt + t] = v[q];
     __syncthreads();
     int span = 1;
     while (span < nt) span <<= 1;
     for (int o = span >> 1; o > 0; o >>= 1) {
-        if (t < o && t + o < nt) scratch[t] = __dadd_rn(scratch[t], scratch[t + o]);
+        if (t < o && t + o < nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) scratch[q * nt + t] = __dadd_rn(scratch[q * nt + t], scratch[q * nt + t + o]);
         __syncthreads();
     }
-    const double r = scratch[0];
-    __syncthreads();
-    return r;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = scratch[q * nt];
 }
 
 // Tile-local cell of a vertex whose cell is this cell stepped back along

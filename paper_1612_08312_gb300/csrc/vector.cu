@@ -292,10 +292,9 @@ __global__ void __launch_bounds__(512) vec_measure_kernel(const __grid_constant_
         }
     }
     const double e = (double)ec, M[3] = {(double)Mc[0], (double)Mc[1], (double)Mc[2]};
-    const double se = tile_sum_f64(e, c.nt, scratch);
-    const double s0 = tile_sum_f64(M[0], c.nt, scratch);
-    const double s1 = tile_sum_f64(M[1], c.nt, scratch);
-    const double s2 = tile_sum_f64(M[2], c.nt, scratch);
+    double tot[4] = {e, M[0], M[1], M[2]};
+    tile_sum4_f64(tot, c.nt, scratch);
+    const double se = tot[0], s0 = tot[1], s1 = tot[2], s2 = tot[3];
     if (threadIdx.x == 0) {
         double *o = B.partials + 4 * (int64_t)blockIdx.x;
         o[0] = se;
@@ -338,7 +337,7 @@ size_t vec_local_smem(const TileShape &t, int prec)
            (size_t)halo_cells(t.TX, t.TY, t.TZ) * 4;
 }
 
-static size_t vec_measure_smem(const TileShape &t) { return (size_t)t.TX * t.TY * t.TZ * sizeof(double); }
+static size_t vec_measure_smem(const TileShape &t) { return (size_t)4 * t.TX * t.TY * t.TZ * sizeof(double); }
 
 template <int NC, typename T>
 struct VecOps {
