@@ -394,13 +394,21 @@ int pyro_graph_set_spins(pyro_graph g, const void *host, size_t bytes);
 /* Canonical cluster labels of the last sweep (N int32; before the first
  * sweep every site is its own cluster). */
 int pyro_graph_get_labels(pyro_graph g, int32_t *host, int64_t n);
+/* The sweep counter that keys the next sweep's random numbers (as
+ * pyro_set_sweep / pyro_get_sweep; the get synchronises and returns 0 for a
+ * NULL handle or a failed read). */
 int pyro_graph_set_sweep(pyro_graph g, uint64_t sweep);
 uint64_t pyro_graph_get_sweep(pyro_graph g);
+/* Sites and bonds of the lattice (0 for a NULL handle). */
 int64_t pyro_graph_num_sites(pyro_graph g);
 int64_t pyro_graph_num_bonds(pyro_graph g);
+/* Wait for the handle's work; PYRO_E_NOCONVERGE if a union hit its bound. */
 int pyro_graph_sync(pyro_graph g);
 void *pyro_graph_get_stream(pyro_graph g);
+/* Kernel launches issued so far (four per Ising sweep, five for n > 1,
+ * two per pyro_graph_measure, one at creation). */
 uint64_t pyro_graph_launch_count(pyro_graph g);
+/* Free the lattice's device memory (after its stream's work) and the handle. */
 void pyro_graph_destroy(pyro_graph g);
 
 #ifdef __cplusplus
