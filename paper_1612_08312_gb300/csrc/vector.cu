@@ -60,6 +60,21 @@ __device__ __forceinline__ void store16(T *p, const T in[16])
     }
 }
 
+// The local kernel's staging area (the halo's projections, then the halo
+// cells' first sites) is dead once the bonds are decided, before the
+// labelling writes its labels and pair list: when it fits in their room
+// (31 words a cell, the start of the core area) it shares it, which halves
+// the shared memory of the FP32 kernels' common tiles.
+__host__ __device__ constexpr size_t vec_stage_bytes(int TX, int TY, int TZ, size_t es)
+{
+    return (size_t)16 * halo_cells(TX, TY, TZ) * es + (size_t)halo_cells(TX, TY, TZ) * 4;
+}
+
+__host__ __device__ constexpr bool vec_stage_shared(int TX, int TY, int TZ, size_t es)
+{
+    return vec_stage_bytes(TX, TY, TZ, es) <= (size_t)31 * TX * TY * TZ * 4;
+}
+
 template <int NC, typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) vec_local_kernel(const __grid_constant__ Batch B)
 {
@@ -69,7 +84,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) vec_local_kernel(
     const Rep &R = B.reps[rep];
     const TileCtx c = tile_ctx(B, R, blockIdx.x - B.tile_begin[rep]);
     const CoreSmem sm = core_smem(smem, c.nt);
-    T *proj = reinterpret_cast<T *>(sm.stage);
+    const bool shared_stage = vec_stage_shared(c.TX, c.TY, c.TZ, sizeof(T));
+    T *proj = reinterpret_cast<T *>(shared_stage ? reinterpret_cast<unsigned char *>(smem) : sm.stage);
     const T *spins = static_cast<const T *>(R.spins);
     const int64_t N = R.N;
     const uint32_t sweep = (uint32_t)R.st->sweep;
@@ -169,6 +185,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) vec_local_kernel(
             act[g] = a;
         }
     }
+    if (shared_stage) __syncthreads();  // the staging area is read no more: the labels may take it
     local_core(c, R, sm, act[0], act[1], act[2], sweep);
 }
 
@@ -332,9 +349,8 @@ void launch_boundary(const Batch &B, int64_t ntiles, cudaStream_t s);
 size_t vec_local_smem(const TileShape &t, int prec)
 {
     const size_t es = prec == PYRO_FP64 ? 8 : 4;
-    // core area, the halo's projections, the halo cells' first sites
-    return core_smem_bytes(t.TX * t.TY * t.TZ) + (size_t)16 * halo_cells(t.TX, t.TY, t.TZ) * es +
-           (size_t)halo_cells(t.TX, t.TY, t.TZ) * 4;
+    const size_t core = core_smem_bytes(t.TX * t.TY * t.TZ);
+    return vec_stage_shared(t.TX, t.TY, t.TZ, es) ? core : core + vec_stage_bytes(t.TX, t.TY, t.TZ, es);
 }
 
 static size_t vec_measure_smem(const TileShape &t) { return (size_t)4 * t.TX * t.TY * t.TZ * sizeof(double); }
