@@ -415,21 +415,29 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
     // together, until each points at its root (no unions any more, so the
     // entries only move up their trees; the work is spread evenly over the
     // threads, whatever the trees' depths)
+    // A representative whose parent is a root (its entry is its own) is
+    // done for good, since no entry changes any more but by these moves: it
+    // leaves the thread's list, so later rounds only walk the deep ones.
     volatile int *vl = s.lab;
+    uint32_t todo = reps;
 #pragma unroll 1
     for (int it = 0; it < 64; ++it) {
         int changed = 0;
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-            if ((reps >> q) & 1u) {
-                const int x = 16 * c.t + q;
-                const int p = vl[lslot(x, nt)];
-                const int gp = vl[lslot(p, nt)];
-                if (gp != p) {
-                    vl[lslot(x, nt)] = gp;
-                    changed = 1;
-                }
+        uint32_t pend = todo;
+#pragma unroll 1
+        while (pend) {
+            const int q = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int x = 16 * c.t + q;
+            const int p = vl[lslot(x, nt)];
+            const int gp = vl[lslot(p, nt)];
+            if (gp != p) {
+                vl[lslot(x, nt)] = gp;
+                changed = 1;
+            } else {
+                todo &= ~(1u << q);
             }
+        }
         if (!__syncthreads_or(changed)) break;
         if (it == 63) atomicOr(&R.st->status, ST_NOCONVERGE);
     }
