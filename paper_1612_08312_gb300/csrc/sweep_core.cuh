@@ -418,10 +418,15 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
     // A representative whose parent is a root (its entry is its own) is
     // done for good, since no entry changes any more but by these moves: it
     // leaves the thread's list, so later rounds only walk the deep ones.
+    // After one such round the representatives left (on deeper chains)
+    // are walked to their roots by their own threads, read-only, and pointed
+    // at them: every entry on the way is an ancestor whatever the other
+    // threads write meanwhile, so one barrier ends the whole resolution.
     volatile int *vl = s.lab;
     uint32_t todo = reps;
+    bool done = false;
 #pragma unroll 1
-    for (int it = 0; it < 64; ++it) {
+    for (int it = 0; it < 1 && !done; ++it) {
         int changed = 0;
         uint32_t pend = todo;
 #pragma unroll 1
@@ -438,8 +443,30 @@ __device__ __forceinline__ void local_core(const TileCtx &c, const Rep &R, const
                 todo &= ~(1u << q);
             }
         }
-        if (!__syncthreads_or(changed)) break;
-        if (it == 63) atomicOr(&R.st->status, ST_NOCONVERGE);
+        done = !__syncthreads_or(changed);  // the same for every thread
+    }
+    if (!done) {
+        bool walked = true;
+#pragma unroll 1
+        while (todo) {
+            const int q = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int x = 16 * c.t + q;
+            int r = vl[lslot(x, nt)];
+#pragma unroll 1
+            for (int st = 0;; ++st) {
+                const int p = vl[lslot(r, nt)];
+                if (p == r) break;
+                r = p;
+                if (st == 16 * nt) {
+                    walked = false;
+                    break;
+                }
+            }
+            vl[lslot(x, nt)] = r;
+        }
+        if (!walked) atomicOr(&R.st->status, ST_NOCONVERGE);
+        __syncthreads();
     }
     // every site takes the root of its component's representative
     uint32_t packed[8];
