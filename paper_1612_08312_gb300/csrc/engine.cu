@@ -1,6 +1,7 @@
 // engine.cu -- host side of a set of lattices updated together: device
 // memory, the replica table, the launch sequence of a sweep, CUDA graphs of
 // multi-sweep chunks, and the per-replica measurement / accumulation kernel.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -28,19 +29,78 @@ void vec_launch_measure(int model, int prec, const Batch &B, int64_t ntiles, cud
 // Eq. 2) and, in mode 1, add them to the Neumaier sums, append the trace
 // record and advance the sweep counter; mode 2 only records them as the last
 // measurement.
+// With B.fold groups per replica, a first kernel sums each group of a
+// replica's tile partials (a contiguous range, fixed order) on its own
+// block, so that the accumulation reads B.fold values per replica instead of
+// one per tile; one block reading tens of thousands of partials, in FP64 for
+// the n-vector models, was the accumulation's whole cost.
+template <bool ISING>
+__global__ void __launch_bounds__(256) fold_kernel(const __grid_constant__ Batch B)
+{
+    const int r = blockIdx.x / B.fold, k = blockIdx.x - r * B.fold;
+    const int64_t b0 = B.tile_begin[r], n = B.tile_begin[r + 1] - b0;
+    const int64_t lo = b0 + n * k / B.fold, hi = b0 + n * (k + 1) / B.fold;
+    const int t = threadIdx.x;
+    if (ISING) {
+        __shared__ unsigned long long su[2][256];
+        unsigned long long a = 0, d = 0;
+        for (int64_t b = lo + t; b < hi; b += blockDim.x) {
+            const unsigned long long *p = reinterpret_cast<const unsigned long long *>(B.partials + 4 * b);
+            a += p[0];
+            d += p[1];
+        }
+        su[0][t] = a;
+        su[1][t] = d;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (t < o) {
+                su[0][t] += su[0][t + o];
+                su[1][t] += su[1][t + o];
+            }
+            __syncthreads();
+        }
+        if (t == 0) {
+            unsigned long long *o = reinterpret_cast<unsigned long long *>(B.folded + 4 * (int64_t)blockIdx.x);
+            o[0] = su[0][0];
+            o[1] = su[1][0];
+        }
+    } else {
+        __shared__ double sv[4][256];
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t b = lo + t; b < hi; b += blockDim.x)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = __dadd_rn(v[q], B.partials[4 * b + q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sv[q][t] = v[q];
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (t < o)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sv[q][t] = __dadd_rn(sv[q][t], sv[q][t + o]);
+            __syncthreads();
+        }
+        if (t == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) B.folded[4 * (int64_t)blockIdx.x + q] = sv[q][0];
+    }
+}
+
 template <bool ISING>
 __global__ void __launch_bounds__(1024) accumulate_kernel(const __grid_constant__ Batch B, int mode, int nc)
 {
     const int r = blockIdx.x;
     const Rep &R = B.reps[r];
     DevStats *st = R.st;
-    const int64_t b0 = B.tile_begin[r], b1 = B.tile_begin[r + 1];
+    // the replica's tile partials, or its folded groups
+    const double *src = B.fold ? B.folded : B.partials;
+    const int64_t b0 = B.fold ? (int64_t)r * B.fold : B.tile_begin[r];
+    const int64_t b1 = B.fold ? (int64_t)(r + 1) * B.fold : B.tile_begin[r + 1];
     double tot[4] = {0.0, 0.0, 0.0, 0.0};
     if (ISING) {
         __shared__ unsigned long long su[2][1024];
         unsigned long long a = 0, d = 0;
         for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
-            const unsigned long long *p = reinterpret_cast<const unsigned long long *>(B.partials + 4 * b);
+            const unsigned long long *p = reinterpret_cast<const unsigned long long *>(src + 4 * b);
             a += p[0];
             d += p[1];
         }
@@ -63,7 +123,7 @@ __global__ void __launch_bounds__(1024) accumulate_kernel(const __grid_constant_
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = __dadd_rn(v[q], B.partials[4 * b + q]);
+            for (int q = 0; q < 4; ++q) v[q] = __dadd_rn(v[q], src[4 * b + q]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) tot[q] = block_sum_f64(v[q]);
         if (threadIdx.x != 0) return;
@@ -232,7 +292,8 @@ size_t workspace_bytes(int R, const int *Ls, int model, int prec, const TileShap
                  ws_align((size_t)ncells * sizeof(uint32_t)) + ws_align((size_t)N * sizeof(int32_t));
         ntiles += ncells / nt;
     }
-    return total + ws_align((size_t)ntiles * 4 * sizeof(double)) + ws_align((size_t)R * sizeof(Rep));
+    return total + ws_align((size_t)(ntiles + (int64_t)R * FOLD_GROUPS) * 4 * sizeof(double)) +
+           ws_align((size_t)R * sizeof(Rep));
 }
 
 // One device array: carved from the caller's workspace when there is one,
@@ -343,7 +404,12 @@ cudaError_t Engine::setup(int R_, const int *Ls, const double *betas, int model_
     }
     B.tile_begin[R] = ntiles;
     B.block_begin[R] = nblocks;
-    e = alloc((void **)&B.partials, (size_t)ntiles * 4 * sizeof(double));
+    // lattices of many tiles first fold their partials (see fold_kernel)
+    int64_t max_tiles = 0;
+    for (int r = 0; r < R; ++r) max_tiles = std::max(max_tiles, B.tile_begin[r + 1] - B.tile_begin[r]);
+    B.fold = max_tiles >= FOLD_MIN_TILES ? FOLD_GROUPS : 0;
+    e = alloc((void **)&B.partials, (size_t)(ntiles + (int64_t)R * FOLD_GROUPS) * 4 * sizeof(double));
+    B.folded = B.partials ? B.partials + 4 * ntiles : nullptr;
     if (e == cudaSuccess) e = alloc((void **)&d_reps, (size_t)R * sizeof(Rep));
     if (e != cudaSuccess) {
         err = ws ? "workspace too small" : "device allocation failed";
@@ -403,6 +469,10 @@ void Engine::enqueue_phase(int p, int mode)
         if (model == PYRO_ISING) ising_launch_measure(B, ntiles, stream);
         else vec_launch_measure(model, prec, B, ntiles, stream);
     } else {
+        if (B.fold) {
+            if (model == PYRO_ISING) fold_kernel<true><<<R * B.fold, 256, 0, stream>>>(B);
+            else fold_kernel<false><<<R * B.fold, 256, 0, stream>>>(B);
+        }
         if (model == PYRO_ISING) accumulate_kernel<true><<<R, 1024, 0, stream>>>(B, mode, 1);
         else accumulate_kernel<false><<<R, 1024, 0, stream>>>(B, mode, model);
     }
@@ -488,9 +558,10 @@ cudaError_t Engine::profile(int n, double *phase_ms)
     return e;
 }
 
-// Kernel launches of one sweep: one per phase, and the crossing phase is
-// two (unions, then the roots' correction bits).
-int Engine::launches_per_sweep() const { return NPHASE + 1; }
+// Kernel launches of one sweep: one per phase, the crossing phase is two
+// (unions, then the roots' correction bits), and the accumulation two when
+// the partials are folded first.
+int Engine::launches_per_sweep() const { return NPHASE + 1 + (B.fold ? 1 : 0); }
 
 cudaGraphExec_t Engine::graph_for(int n)
 {

@@ -13,6 +13,10 @@ constexpr int GRAPH_CHUNK = 32;
 // Phases of a sweep: tile-local labelling, crossing unions (two launches),
 // flip, measurement, accumulation.
 constexpr int NPHASE = 5;
+// A lattice of at least FOLD_MIN_TILES tiles has its measurement partials
+// summed in FOLD_GROUPS groups on as many blocks before the accumulation.
+constexpr int FOLD_MIN_TILES = 2048;
+constexpr int FOLD_GROUPS = 64;
 
 struct GraphEntry {
     int n;

@@ -146,6 +146,10 @@ struct Batch {
     int lTX, lTY, lTZ;  // log2 of the (power-of-two) tile edges
     int64_t tile_begin[MAX_REPS + 1];
     int64_t block_begin[MAX_REPS + 1];
+    // last, so that the fields the sweep kernels read keep their offsets
+    // (moving them measurably slowed the local and crossing kernels)
+    double *folded;    // 4 per group of a replica's partials (fold groups per replica), or unused
+    int fold;          // groups per replica the partials are first summed into; 0 = none
 };
 
 __device__ __forceinline__ int find_rep(const int64_t *begin, int R, int64_t blk)
