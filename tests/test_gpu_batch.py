@@ -49,6 +49,24 @@ def test_batch_graph_chunks_and_launch_accounting():
     assert s["count"] == 70
 
 
+def test_folded_accumulation_matches_the_oracle_and_counts_its_launch():
+    """A lattice of 2048 tiles or more sums its measurement partials in
+    groups first (one more launch per sweep); its statistics must still be
+    the oracle's, bit for bit."""
+    L = 32
+    g = pyro.Lattice(L, pyro.ISING, 5, start="random", tile=(4, 2, 2))  # 32^3 / 16 = 2048 tiles
+    o = oracle.Oracle(L, oracle.ISING, 5, "random")
+    l0 = g.launches
+    g.set_graphs(False)
+    g.sweep(1 / 4.21394, 3)
+    g.sync()
+    assert g.launches - l0 == 3 * 7
+    o.sweep(1 / 4.21394, 3)
+    assert g.stats() == o.stats()
+    assert g.measure() == o.measure()
+    g.close()
+
+
 def test_mixed_sizes_uneven_tiles():
     Ls = [16, 24, 32]
     b = pyro.Replicas(Ls, [1 / 4.21394] * 3, pyro.ISING, start="random", seed=2)
