@@ -56,12 +56,13 @@ def test_folded_accumulation_matches_the_oracle_and_counts_its_launch():
     L = 32
     g = pyro.Lattice(L, pyro.ISING, 5, start="random", tile=(4, 2, 2))  # 32^3 / 16 = 2048 tiles
     o = oracle.Oracle(L, oracle.ISING, 5, "random")
-    l0 = g.launches
     g.set_graphs(False)
+    g.sweep(1 / 4.21394, 1)  # the first sweep at a new beta also sets the lattice's parameters
+    l0 = g.launches
     g.sweep(1 / 4.21394, 3)
     g.sync()
     assert g.launches - l0 == 3 * 7
-    o.sweep(1 / 4.21394, 3)
+    o.sweep(1 / 4.21394, 4)
     assert g.stats() == o.stats()
     assert g.measure() == o.measure()
     g.close()
