@@ -100,3 +100,44 @@ def test_workspace_bytes_is_host_only_and_checks_its_config():
         pyro.pyro_workspace_bytes(0, pyro.ISING)
     with pytest.raises(pyro.PyroError):
         pyro.pyro_workspace_bytes(8, pyro.ISING, tile=(3, 1, 1))
+
+
+def test_graph_bonds_from_table_on_the_host():
+    """pyro_graph_bonds_from_table runs on the host: the simple-cubic table
+    gives the oracle's bond list, and bad tables are refused."""
+    import numpy as np
+    import oracle
+    L = 4
+    bi, bj = oracle.sc_edges(L)
+    rows = [[] for _ in range(L ** 3)]
+    for a, b in zip(bi.tolist(), bj.tolist()):
+        rows[a].append(b)
+        rows[b].append(a)
+    nbr = np.full((L ** 3, 7), -1, dtype=np.int32)  # one spare empty column
+    for i, r in enumerate(rows):
+        nbr[i, :len(r)] = r
+    gi, gj = pyro.pyro_graph_bonds_from_table(nbr)
+    oi, oj = oracle.edges_from_table(nbr)
+    assert (gi == oi).all() and (gj == oj).all() and len(gi) == 3 * L ** 3
+    for bad in ([[0, -1], [0, -1]], [[1, -1], [-1, -1]], [[5, -1], [0, -1]]):  # self entry, asymmetric, out of range
+        with pytest.raises(pyro.PyroError) as ei:
+            pyro.pyro_graph_bonds_from_table(np.array(bad, dtype=np.int32))
+        assert ei.value.code == pyro.E_INVAL
+
+
+def test_graph_init_rejects_bad_arguments_on_the_host():
+    import numpy as np
+    cases = [dict(model=4, sc_L=8), dict(model=1, sc_L=1), dict(model=1, sc_L=1291),
+             dict(model=1, nsites=3, bond_i=np.array([0]), bond_j=np.array([0])),      # self-loop
+             dict(model=1, nsites=3, bond_i=np.array([0]), bond_j=np.array([3])),      # out of range
+             dict(model=1, sc_L=8, bond_i=np.array([0]), bond_j=np.array([1])),        # list with sc_L
+             dict(model=2, precision=5, sc_L=8), dict(model=1, sc_L=8, start=3), dict(model=1, sc_L=8, J=-1.0),
+             dict(model=1, nsites=0)]
+    for kw in cases:
+        with pytest.raises(pyro.PyroError) as ei:
+            pyro.pyro_graph_init(kw.pop("model"), 1, **kw)
+        assert ei.value.code == pyro.E_INVAL, kw
+    L = pyro.lib()
+    assert L.pyro_graph_sweep(None, 0.2, 1) == pyro.E_INVAL
+    assert L.pyro_graph_num_sites(None) == 0
+    L.pyro_graph_destroy(None)
