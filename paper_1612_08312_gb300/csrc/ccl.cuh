@@ -25,7 +25,9 @@ __device__ __forceinline__ int lslot(int v, int nt) { return (v & 15) * nt + (v 
 static __constant__ int c_unite_bound = 4096;
 
 // Union of the clusters of a and b in shared memory.  Both finds walk in
-// lockstep (path splitting), so their shared-memory loads overlap.
+// lockstep, so their shared-memory loads overlap; they write nothing on the
+// way (path-halving writes were measured slower: the final resolution of
+// the representatives shortens the trees once, for all of them).
 // Returns false if the iteration bound was hit.
 __device__ __forceinline__ bool sunite(int *lab, int a, int b, int nt)
 {
@@ -38,13 +40,11 @@ __device__ __forceinline__ bool sunite(int *lab, int a, int b, int nt)
         for (int st = 0; (pa != a || pb != b) && st < 65536; ++st) {
             if (pa != a) {
                 const int g = vl[lslot(pa, nt)];
-                if (g != pa) vl[lslot(a, nt)] = g;
                 a = pa;
                 pa = g;
             }
             if (pb != b) {
                 const int g = vl[lslot(pb, nt)];
-                if (g != pb) vl[lslot(b, nt)] = g;
                 b = pb;
                 pb = g;
             }
