@@ -54,3 +54,27 @@ def test_committed_traffic_is_read_per_kernel_and_fingerprint(tmp_path):
         assert bench.committed_traffic("ising_measure_kernel", 1000) is None
     finally:
         bench.ROOT = old
+
+
+def test_generic_workload_inputs_and_bytes():
+    """The generic-lattice workloads' inputs: the explicit simple-cubic bond
+    list handed to the library is the oracle's, site masks are seeded and
+    have the stated occupation, and the algorithmic bytes per site follow
+    the stated model (14 B, plus 8 B per listed bond)."""
+    import numpy as np
+    import oracle
+    import workloads
+    for L in (3, 4, 6):
+        a = workloads.sc_bond_list(L)
+        b = oracle.sc_edges(L)
+        assert (a[0] == b[0]).all() and (a[1] == b[1]).all()
+    m1 = workloads.site_mask(100000, 0.8, 7)
+    m2 = workloads.site_mask(100000, 0.8, 7)
+    assert (m1 == m2).all() and abs(m1.mean() - 0.8) < 0.01 and m1.dtype == np.uint8
+    assert bench.graph_bytes_per_site(bench.WORKLOADS["sc_L640"]) == 14.0
+    assert bench.graph_bytes_per_site(bench.WORKLOADS["sc_list_L512"]) == 14.0 + 24.0
+    for name in ("sc_L640", "sc_dil_L512", "sc_list_L512"):
+        wl = bench.WORKLOADS[name]
+        assert wl["model"] == 1 and wl["lattice"] in ("sc", "list")
+    # the simple-cubic L = 640 lattice has about the pyrochlore L = 256 site count
+    assert abs(640 ** 3 / (16 * 256 ** 3) - 1) < 0.03
