@@ -11,7 +11,9 @@ Each pin comes from outside the oracle itself:
     occupied sub-lattice;
   - on rings the Ising energy and <M^2> have closed forms (transfer
     matrix), and the XY and Heisenberg energies per bond are I1/I0 and the
-    Langevin function, up to corrections of order u^N."""
+    Langevin function, up to corrections of order u^N;
+  - on a small diluted graph the chain samples the Boltzmann distribution
+    of its occupied part, enumerated exactly."""
 import numpy as np
 import pytest
 
@@ -187,3 +189,36 @@ def test_vector_ring_energy(model, beta):
     u = special.i1(beta) / special.i0(beta) if model == 2 else 1 / np.tanh(beta) - 1 / beta
     Em, Ee = _binned_mean(tr[:, 0])
     assert abs(Em + N * u) < 5 * Ee + 1e-6
+
+
+def test_diluted_graph_samples_the_boltzmann_distribution_of_its_occupied_part():
+    """On a small irregular graph with a vacant site and a masked bond, the
+    chain's states of the occupied sites are distributed as exp(-beta E)
+    with E over the present bonds only (exact enumeration), and the vacant
+    site's spin never changes."""
+    edges = [(0, 1), (1, 2), (2, 3), (3, 0), (0, 2), (3, 4), (4, 5), (1, 5)]
+    bi = np.array([e[0] for e in edges], dtype=np.int32)
+    bj = np.array([e[1] for e in edges], dtype=np.int32)
+    site = np.array([1, 1, 1, 1, 0, 1], dtype=np.uint8)
+    bond = np.array([1, 1, 1, 1, 0, 1, 1, 1], dtype=np.uint8)  # (0, 2) absent
+    present = [e for k, e in enumerate(edges) if bond[k] and site[e[0]] and site[e[1]]]
+    occ = [i for i in range(6) if site[i]]
+    beta = 0.6
+    g = oracle.GraphOracle(6, bi, bj, 1, 31, "random", site_mask=site, edge_mask=bond)
+    s4 = g.spins()[4]
+    n = 60000
+    counts = np.zeros(2 ** len(occ))
+    for _ in range(n):
+        g.sweep(beta)
+        s = g.spins()
+        assert s[4] == s4
+        counts[sum(((1 - s[i]) // 2) << k for k, i in enumerate(occ))] += 1
+    E = np.zeros(2 ** len(occ))
+    for a in range(2 ** len(occ)):
+        sig = {i: 1 - 2 * ((a >> k) & 1) for k, i in enumerate(occ)}
+        E[a] = -sum(sig[i] * sig[j] for i, j in present)
+    pi = np.exp(-beta * (E - E.min()))
+    pi /= pi.sum()
+    f = counts / n
+    sigma = np.sqrt(pi * (1 - pi) / (n / 4))  # a generous autocorrelation allowance
+    assert (np.abs(f - pi) < 5 * sigma + 1e-4).all()
